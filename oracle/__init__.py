@@ -49,6 +49,7 @@ class Params(ctypes.Structure):
         ("r", ctypes.c_int), ("rn", ctypes.c_int), ("T", ctypes.c_int), ("stride", ctypes.c_int),
         ("k", ctypes.c_double), ("reject", ctypes.c_int), ("reject_ratio", ctypes.c_double),
         ("det_tol", ctypes.c_double), ("pivot_tol", ctypes.c_double), ("min_window", ctypes.c_int),
+        ("perturb", ctypes.c_double), ("perturb_points", ctypes.c_double), ("perturb_seed", ctypes.c_ulonglong),
     ]
 
 
@@ -58,22 +59,23 @@ class Result(ctypes.Structure):
         ("k1", ctypes.c_double), ("k2", ctypes.c_double),
         ("normal", ctypes.c_double * 3), ("n0", ctypes.c_double * 3),
         ("A", ctypes.c_double), ("B", ctypes.c_double), ("C", ctypes.c_double), ("tz", ctypes.c_double),
-        ("R", ctypes.c_double * 9), ("min_pivot", ctypes.c_double),
+        ("R", ctypes.c_double * 9), ("min_pivot", ctypes.c_double), ("last_b", ctypes.c_double * 6),
     ]
 
 
 # validity thresholds of the method as this repository reads it (both the
 # oracle and the CUDA path use the same values, each from its own source)
 DET_TOL = 1e-6
-PIVOT_TOL = 1e-7
+PIVOT_TOL = 1e-5
 MIN_WINDOW = 6
 
 
 def params(fx, fy, cx, cy, r, T, *, rn=3, k=1e-4, stride=1, reject=0, reject_ratio=2.0,
-           det_tol=DET_TOL, pivot_tol=PIVOT_TOL, min_window=MIN_WINDOW) -> Params:
+           det_tol=DET_TOL, pivot_tol=PIVOT_TOL, min_window=MIN_WINDOW, perturb=0.0,
+           perturb_points=0.0, perturb_seed=0) -> Params:
     return Params(float(fx), float(fy), float(cx), float(cy), int(r), int(rn), int(T), int(stride),
                   float(k), int(reject), float(reject_ratio), float(det_tol), float(pivot_tol),
-                  int(min_window))
+                  int(min_window), float(perturb), float(perturb_points), int(perturb_seed))
 
 
 _lib = None
@@ -102,10 +104,10 @@ def lib():
         L.or_fit_pixel_f32.argtypes = [_F, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(Result)]
         for name, dp in (("or_curvature_image", _F), ("or_curvature_image_f64", _D)):
-            getattr(L, name).argtypes = [dp, ctypes.c_int, ctypes.c_int, _P, _D, _D, _D, _I, _D, ctypes.c_int]
+            getattr(L, name).argtypes = [dp, ctypes.c_int, ctypes.c_int, _P, _D, _D, _D, _I, _D, _D, ctypes.c_int]
         for name, dp in (("or_curvature_pixels", _F), ("or_curvature_pixels_f64", _D)):
             getattr(L, name).argtypes = [dp, ctypes.c_int, ctypes.c_int, _P, _I, ctypes.c_int,
-                                         _D, _D, _D, _I, _D, ctypes.c_int]
+                                         _D, _D, _D, _I, _D, _D, ctypes.c_int]
         L.or_max_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -218,6 +220,16 @@ class Field:
     normal: np.ndarray
     status: np.ndarray
     min_pivot: np.ndarray
+    last_b: np.ndarray      # update b of the last iteration, (..., 6)
+
+    def converged(self, step_k=1e-5, step_theta=1e-6):
+        """Pixels whose last Gauss-Newton update is below step_k * (1 + |k1|)
+        for A, B, C and below step_theta (rad) for the frame: the fixed-count
+        iteration has settled, so its output no longer depends on the path."""
+        kk = np.abs(self.last_b[..., 3:]).max(-1)
+        th = np.hypot(self.last_b[..., 0], self.last_b[..., 1])
+        with np.errstate(invalid="ignore"):
+            return (self.status == OK) & (kk <= step_k * (1 + np.abs(self.k1))) & (th <= step_theta)
 
 
 def curvature_image(depth, p: Params, nthreads: int = 0) -> Field:
@@ -227,15 +239,16 @@ def curvature_image(depth, p: Params, nthreads: int = 0) -> Field:
     H, W = depth.shape
     k1, k2 = np.zeros((H, W)), np.zeros((H, W))
     nrm, st, mp = np.zeros((H, W, 3)), np.zeros((H, W), dtype=np.int32), np.zeros((H, W))
+    lb = np.zeros((H, W, 6))
     if depth.dtype == np.float32:
         d = np.ascontiguousarray(depth)
         lib().or_curvature_image(d.ctypes.data_as(_F), H, W, ctypes.byref(p), _dp(k1), _dp(k2), _dp(nrm),
-                                 _ip(st), _dp(mp), nthreads)
+                                 _ip(st), _dp(mp), _dp(lb), nthreads)
     else:
         d = _as_f64(depth)
         lib().or_curvature_image_f64(_dp(d), H, W, ctypes.byref(p), _dp(k1), _dp(k2), _dp(nrm), _ip(st),
-                                     _dp(mp), nthreads)
-    return Field(k1, k2, nrm, st, mp)
+                                     _dp(mp), _dp(lb), nthreads)
+    return Field(k1, k2, nrm, st, mp, lb)
 
 
 def curvature_pixels(depth, p: Params, uv, nthreads: int = 0) -> Field:
@@ -246,12 +259,13 @@ def curvature_pixels(depth, p: Params, uv, nthreads: int = 0) -> Field:
     n = uv.shape[0]
     k1, k2 = np.zeros(n), np.zeros(n)
     nrm, st, mp = np.zeros((n, 3)), np.zeros(n, dtype=np.int32), np.zeros(n)
+    lb = np.zeros((n, 6))
     if depth.dtype == np.float32:
         d = np.ascontiguousarray(depth)
         lib().or_curvature_pixels(d.ctypes.data_as(_F), H, W, ctypes.byref(p), _ip(uv), n, _dp(k1), _dp(k2),
-                                  _dp(nrm), _ip(st), _dp(mp), nthreads)
+                                  _dp(nrm), _ip(st), _dp(mp), _dp(lb), nthreads)
     else:
         d = _as_f64(depth)
         lib().or_curvature_pixels_f64(_dp(d), H, W, ctypes.byref(p), _ip(uv), n, _dp(k1), _dp(k2), _dp(nrm),
-                                      _ip(st), _dp(mp), nthreads)
-    return Field(k1, k2, nrm, st, mp)
+                                      _ip(st), _dp(mp), _dp(lb), nthreads)
+    return Field(k1, k2, nrm, st, mp, lb)

@@ -76,6 +76,10 @@ typedef struct {
     double det_tol;        /* initial normal degenerate when det M <= det_tol (tr M)^2 */
     double pivot_tol;      /* normal equations singular when a scaled pivot <= pivot_tol */
     int min_window;        /* fewest valid window points accepted */
+    double perturb;        /* sensitivity probe: relative noise on the normal equations and on
+                              the initial-normal sums (0 = off) */
+    double perturb_points; /* sensitivity probe: relative noise on each p' coordinate (0 = off) */
+    unsigned long long perturb_seed;
 } or_params;
 
 typedef struct {
@@ -88,6 +92,7 @@ typedef struct {
     double A, B, C, tz;  /* final quadric and offset */
     double R[9];         /* final rotation, row major, camera -> local */
     double min_pivot;    /* smallest scaled Cholesky pivot over all iterations */
+    double last_b[6];    /* the update b of the last iteration (0 when T = 0) */
 } or_result;
 
 /* ------------------------------------------------------------------------ */
@@ -143,10 +148,54 @@ OR_EXPORT void or_backproject(const or_params* p, int u, int v, double z, double
 }
 
 /* ------------------------------------------------------------------------ */
+/* sensitivity probe (not part of the method)                                */
+
+/* SplitMix64 finaliser (Steele, Lea, Flood 2014): a counter-based generator,
+ * so a noise value depends only on its key (pixel, iteration, entry, seed). */
+static unsigned long long splitmix64(unsigned long long x) {
+    x += 0x9E3779B97F4A7C15ULL;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+    return x ^ (x >> 31);
+}
+
+/* uniform in [-1, 1) */
+static double noise_at(unsigned long long key) {
+    return (double)(splitmix64(key) >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+/* The probe multiplies chosen intermediate values by 1 + a x, x uniform in
+ * [-1, 1) keyed by (pixel, iteration, entry, seed): each entry of the
+ * symmetric normal matrix and of the right-hand side (a = perturb), the
+ * sums M and v of the initial-normal regression (a = perturb) and each
+ * coordinate of p' (a = perturb_points).  The method's output under this noise
+ * tells how much rounding of that relative size can move it: the tests use it
+ * to find the pixels whose answer is fixed at single precision. */
+static void perturb_system(const or_params* p, unsigned long long key, double N[36], double rhs[6]) {
+    if (!(p->perturb > 0.0)) return;
+    for (int a = 0; a < 6; a++) {
+        for (int c = a; c < 6; c++) {
+            const double f = 1.0 + p->perturb * noise_at(key * 64 + (unsigned long long)(6 * a + c));
+            N[6 * a + c] *= f;
+            if (c != a) N[6 * c + a] *= f;
+        }
+        rhs[a] *= 1.0 + p->perturb * noise_at(key * 64 + 36 + (unsigned long long)a);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* step 2: initial normal (Sec. 3.2.1, Eq. initialnormal)                   */
+
+static int initial_normal_keyed(const double* depth, int H, int W, const or_params* p, int u0,
+                                int v0, double n[3], unsigned long long key);
 
 OR_EXPORT int or_initial_normal(const double* depth, int H, int W, const or_params* p, int u0,
                                 int v0, double n[3]) {
+    return initial_normal_keyed(depth, H, W, p, u0, v0, n, p->perturb_seed);
+}
+
+static int initial_normal_keyed(const double* depth, int H, int W, const or_params* p, int u0,
+                                int v0, double n[3], unsigned long long key) {
     const int rn = p->rn;
     double P[3], sx = 0.0, sy = 0.0, sz = 0.0;
     int cnt = 0;
@@ -173,6 +222,13 @@ OR_EXPORT int or_initial_normal(const double* depth, int H, int W, const or_para
             m00 += dx * dx; m01 += dx * dy; m11 += dy * dy;
             v0s += dx * dz; v1s += dy * dz;
         }
+    if (p->perturb > 0.0) {
+        m00 *= 1.0 + p->perturb * noise_at(key * 64 + 50);
+        m01 *= 1.0 + p->perturb * noise_at(key * 64 + 51);
+        m11 *= 1.0 + p->perturb * noise_at(key * 64 + 52);
+        v0s *= 1.0 + p->perturb * noise_at(key * 64 + 53);
+        v1s *= 1.0 + p->perturb * noise_at(key * 64 + 54);
+    }
     const double det = m00 * m11 - m01 * m01, tr = m00 + m11;
     if (!(det > p->det_tol * tr * tr)) return OR_BAD_NORMAL;
     /* (a, b)^T = M^-1 v by the 2x2 inverse */
@@ -335,9 +391,20 @@ static int solve6(const double N[36], const double rhs[6], double tol, double b[
  * (theta_x, theta_y, t_z, A, B, C) <- (...) - b, the rotation part applied as
  * R <- Rot(-b_0, -b_1, 0) R.  Optional outputs N (36), rhs (6), b (6) and the
  * weights (m).  Returns OR_OK or OR_SINGULAR (state then unchanged). */
+static int irls_step_keyed(const double* pts, int m, const or_params* p, double R[9], double* tz,
+                           double* A, double* B, double* C, double* min_pivot, double* N_out,
+                           double* rhs_out, double* b_out, double* w_out, unsigned long long key);
+
 OR_EXPORT int or_irls_step(const double* pts, int m, const or_params* p, double R[9], double* tz,
                            double* A, double* B, double* C, double* min_pivot, double* N_out,
                            double* rhs_out, double* b_out, double* w_out) {
+    return irls_step_keyed(pts, m, p, R, tz, A, B, C, min_pivot, N_out, rhs_out, b_out, w_out,
+                           p->perturb_seed);
+}
+
+static int irls_step_keyed(const double* pts, int m, const or_params* p, double R[9], double* tz,
+                           double* A, double* B, double* C, double* min_pivot, double* N_out,
+                           double* rhs_out, double* b_out, double* w_out, unsigned long long key) {
     double N[36], rhs[6], b[6], mp = 1.0;
     double* eps = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     double* J = (double*)malloc(sizeof(double) * 6 * (size_t)(m > 0 ? m : 1));
@@ -360,6 +427,7 @@ OR_EXPORT int or_irls_step(const double* pts, int m, const or_params* p, double 
     }
     free(eps);
     free(J);
+    perturb_system(p, key, N, rhs);
     if (N_out) memcpy(N_out, N, sizeof N);
     if (rhs_out) memcpy(rhs_out, rhs, sizeof rhs);
     const int st = solve6(N, rhs, p->pivot_tol, b, &mp);
@@ -429,8 +497,13 @@ OR_EXPORT int or_fit_pixel(const double* depth, int H, int W, const or_params* p
     res->min_pivot = 1.0;
     const double z0 = depth[(size_t)v0 * W + u0];
     if (!range_valid(z0)) { fail(res, OR_INVALID_CENTRE); return res->status; }
+    const unsigned long long pkey =
+        splitmix64(p->perturb_seed ^ splitmix64(((unsigned long long)v0 << 32) ^ (unsigned long long)u0));
     double n[3];
-    if (or_initial_normal(depth, H, W, p, u0, v0, n) != OR_OK) { fail(res, OR_BAD_NORMAL); return res->status; }
+    if (initial_normal_keyed(depth, H, W, p, u0, v0, n, pkey * 1024) != OR_OK) {
+        fail(res, OR_BAD_NORMAL);
+        return res->status;
+    }
     memcpy(res->n0, n, sizeof n);
     double R[9], tz = 0.0, A = 0.0, B = 0.0, C = 0.0;
     or_frame_from_normal(n, R);
@@ -448,11 +521,16 @@ OR_EXPORT int or_fit_pixel(const double* depth, int H, int W, const or_params* p
         const int u = uv[2 * i], v = uv[2 * i + 1];
         or_backproject(p, u, v, depth[(size_t)v * W + u], Pi);
         for (int c = 0; c < 3; c++) pts[3 * i + c] = Pi[c] - P0[c];
+        if (p->perturb_points > 0.0)
+            for (int c = 0; c < 3; c++)
+                pts[3 * i + c] *= 1.0 + p->perturb_points *
+                                           noise_at((pkey * 1024 + 512) * 4096 + (unsigned long long)(3 * i + c));
     }
     free(uv);
     double mp = 1.0;
     for (int t = 0; t < p->T; t++) {
-        if (or_irls_step(pts, m, p, R, &tz, &A, &B, &C, &mp, NULL, NULL, NULL, NULL) != OR_OK) {
+        const unsigned long long key = pkey * 1024 + 1 + (unsigned long long)t;
+        if (irls_step_keyed(pts, m, p, R, &tz, &A, &B, &C, &mp, NULL, NULL, res->last_b, NULL, key) != OR_OK) {
             free(pts);
             res->min_pivot = mp;
             res->iters = t;
@@ -476,7 +554,8 @@ OR_EXPORT int or_fit_pixel(const double* depth, int H, int W, const or_params* p
 /* whole images                                                              */
 
 static void store(const or_result* r, size_t i, double* k1, double* k2, double* normal,
-                  int* status, double* min_pivot) {
+                  int* status, double* min_pivot, double* last_b) {
+    if (last_b) for (int c = 0; c < 6; c++) last_b[6 * i + c] = r->last_b[c];
     if (k1) k1[i] = r->k1;
     if (k2) k2[i] = r->k2;
     if (normal) for (int c = 0; c < 3; c++) normal[3 * i + c] = r->normal[c];
@@ -502,18 +581,18 @@ OR_EXPORT int or_max_threads(void) {
 }
 
 /* All pixels of a double-precision range image; outputs are H*W (normal
- * H*W*3), any of them may be NULL.  Pixels are independent; nthreads > 0 sets
- * the OpenMP thread count. */
+ * H*W*3, last_b H*W*6), any of them may be NULL.  Pixels are independent;
+ * nthreads > 0 sets the OpenMP thread count. */
 OR_EXPORT void or_curvature_image_f64(const double* depth, int H, int W, const or_params* p,
                                       double* k1, double* k2, double* normal, int* status,
-                                      double* min_pivot, int nthreads) {
+                                      double* min_pivot, double* last_b, int nthreads) {
     set_threads(nthreads);
     const long npx = (long)H * W;
 #pragma omp parallel for schedule(dynamic, 8)
     for (long i = 0; i < npx; i++) {
         or_result r;
         or_fit_pixel(depth, H, W, p, (int)(i % W), (int)(i / W), &r);
-        store(&r, (size_t)i, k1, k2, normal, status, min_pivot);
+        store(&r, (size_t)i, k1, k2, normal, status, min_pivot, last_b);
     }
 }
 
@@ -521,13 +600,13 @@ OR_EXPORT void or_curvature_image_f64(const double* depth, int H, int W, const o
 OR_EXPORT void or_curvature_pixels_f64(const double* depth, int H, int W, const or_params* p,
                                        const int* uv, int n, double* k1, double* k2,
                                        double* normal, int* status, double* min_pivot,
-                                       int nthreads) {
+                                       double* last_b, int nthreads) {
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 8)
     for (int i = 0; i < n; i++) {
         or_result r;
         or_fit_pixel(depth, H, W, p, uv[2 * i], uv[2 * i + 1], &r);
-        store(&r, (size_t)i, k1, k2, normal, status, min_pivot);
+        store(&r, (size_t)i, k1, k2, normal, status, min_pivot, last_b);
     }
 }
 
@@ -540,17 +619,17 @@ static double* widen(const float* d, long npx) {
 
 OR_EXPORT void or_curvature_image(const float* depth, int H, int W, const or_params* p, double* k1,
                                   double* k2, double* normal, int* status, double* min_pivot,
-                                  int nthreads) {
+                                  double* last_b, int nthreads) {
     double* d = widen(depth, (long)H * W);
-    or_curvature_image_f64(d, H, W, p, k1, k2, normal, status, min_pivot, nthreads);
+    or_curvature_image_f64(d, H, W, p, k1, k2, normal, status, min_pivot, last_b, nthreads);
     free(d);
 }
 
 OR_EXPORT void or_curvature_pixels(const float* depth, int H, int W, const or_params* p,
                                    const int* uv, int n, double* k1, double* k2, double* normal,
-                                   int* status, double* min_pivot, int nthreads) {
+                                   int* status, double* min_pivot, double* last_b, int nthreads) {
     double* d = widen(depth, (long)H * W);
-    or_curvature_pixels_f64(d, H, W, p, uv, n, k1, k2, normal, status, min_pivot, nthreads);
+    or_curvature_pixels_f64(d, H, W, p, uv, n, k1, k2, normal, status, min_pivot, last_b, nthreads);
     free(d);
 }
 

@@ -329,3 +329,13 @@ def kinect_scene(seed: int = 0, H: int = 480, W: int = 640, noise: str = "kinect
             prims.append(Saddle(c, _rand_rotation(rng, np.deg2rad(45)), a, cc, 0.1))
     nf = {"kinect": kinect_noise, "tof": tof_noise, "none": None}[noise]
     return render(cam, prims, noise=nf, rng=rng, invalid_frac=invalid_frac)
+
+
+def crop(scene: Scene, v0: int, u0: int, H: int, W: int) -> Scene:
+    """The H x W window of a scene starting at row v0, column u0, with the
+    principal point moved so that every pixel keeps its ray."""
+    c = scene.cam
+    cam = Camera(H, W, c.fx, c.fy, c.cx - u0, c.cy - v0)
+    sl = (slice(v0, v0 + H), slice(u0, u0 + W))
+    return Scene(np.ascontiguousarray(scene.depth[sl]), cam, scene.gt_k1[sl], scene.gt_k2[sl],
+                 scene.gt_normal[sl], scene.label[sl], scene.clean[sl], scene.prims)
