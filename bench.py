@@ -1,0 +1,347 @@
+"""Throughput of dense per-pixel principal curvature on synthetic Kinect-like
+range images: 640 x 480, window radius 7 (15 x 15), 5 re-weighted iterations,
+FP32 (the per-pixel quadric fit of Spek, Li, Drummond, arXiv 1707.00385).
+
+One step = the whole method (back-projection, initial normal, 5 iterations,
+eigen step, refined normal) over a batch of FRAMES distinct frame buffers
+(about 157 MB of ranges, more than the 129 MB L2, so no step reads another's
+inputs from L2), one pc_compute launch per frame.
+
+Prints one JSON line.  `value` is Mpixel/s over the device-timed region with
+inputs resident in HBM; `e2e` is the same metric through pc_compute_host with
+pinned host buffers (host-to-device ranges and device-to-host k1, k2, normals
+inside the timed region); `roofline` reports the kernel against the FP32 ALU
+peak; `cpu_baseline` times the FP64 oracle on a bounded sample on the host.
+
+--impl reference times the oracle alone, on the host cores, on the same
+workload (each step a bounded sample).
+
+Multi-GPU (torchrun): every rank runs the same per-rank workload on its own
+GPU (replicas; the method needs no exchange), timing is bracketed by barriers
+and the max over ranks is reported (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H, W, RADIUS, ITERS = 480, 640, 7, 5
+FRAMES = 128          # frame buffers per step
+SCENES = 8            # distinct seeded scenes (seeds 0..7), repeated over the buffers
+FLOP_PER_VISIT = 101  # counted FP32 operations per window point per iteration
+FLOP_PER_SOLVE = 250  # per pixel per iteration (6x6 system, update)
+FLOP_PER_NORMAL_PT = 12
+FP32_LANES_PER_SM = 128
+METRIC = ("Mpixel/s of (k1,k2) at 640x480 r=7 vs FP32 roofline; "
+          "served frames/s + p99 at <=1e-3 rel err")
+WORKLOAD = "640x480 Kinect-like synthetic scenes, window radius 7 (15x15), 5 IRLS iterations, FP32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=FRAMES)
+    ap.add_argument("--scenes", type=int, default=SCENES)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def scenes(n):
+    import synth
+    return [synth.kinect_scene(seed) for seed in range(n)]
+
+
+def counted_flop(depth, r=RADIUS, T=ITERS, rn=3):
+    """Counted FP32 work of one frame: for every pixel with a valid range and
+    enough valid neighbours, T * (101 |W_p| + 250) + 12 |N_p|, where |W_p| and
+    |N_p| are the valid points of its (2r+1)^2 window and (2rn+1)^2 patch."""
+    valid = (depth > 0) & np.isfinite(depth)
+    v = valid.astype(np.int64)
+
+    def box(rad):
+        c = np.pad(v, ((1, 0), (1, 0))).cumsum(0).cumsum(1)
+        Hh, Ww = v.shape
+        y0 = np.clip(np.arange(Hh) - rad, 0, Hh)
+        y1 = np.clip(np.arange(Hh) + rad + 1, 0, Hh)
+        x0 = np.clip(np.arange(Ww) - rad, 0, Ww)
+        x1 = np.clip(np.arange(Ww) + rad + 1, 0, Ww)
+        return c[y1][:, x1] - c[y0][:, x1] - c[y1][:, x0] + c[y0][:, x0]
+
+    nw, nn = box(r), box(rn)
+    use = valid & (nw >= 6) & (nn >= 3)
+    return float(np.sum(np.where(use, T * (FLOP_PER_VISIT * nw + FLOP_PER_SOLVE) + FLOP_PER_NORMAL_PT * nn, 0)))
+
+
+def kernel_sources_hash():
+    d = os.path.join(ROOT, "paper_1707_00385_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "k_fit_r7_640x480_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kv = dict(l.strip().split("=", 1) for l in open(p) if "=" in l and not l.startswith("#"))
+    if kv.get("kernel_sources_sha256_16") != kernel_sources_hash():
+        return None
+    return float(kv["dram_bytes_per_launch"])
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(frames_np, intr, seconds):
+    """The FP64 oracle as it stands on the host cores, on rows of the first
+    frame(s) until about `seconds` of work: Mpixel/s."""
+    import oracle
+    p = oracle.params(*intr, r=RADIUS, T=ITERS)
+    cores = oracle.max_threads()
+    done, t0 = 0, time.perf_counter()
+    rows = 8
+    fi, v0 = 0, 0
+    while time.perf_counter() - t0 < seconds and fi < len(frames_np):
+        d = frames_np[fi]
+        vv, uu = np.mgrid[v0:min(v0 + rows, H), 0:W]
+        uv = np.stack([uu.ravel(), vv.ravel()], 1)
+        oracle.curvature_pixels(d, p, uv, nthreads=cores)
+        done += uv.shape[0]
+        v0 += rows
+        if v0 >= H:
+            fi, v0 = fi + 1, 0
+    dt = time.perf_counter() - t0
+    return {"value": done / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} pixels ({done // W} rows of 640x480 seeded scenes), "
+                      f"FP64 C oracle, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    frames = [s.depth for s in scenes(1)]
+    intr = (525.0, 525.0, 319.5, 239.5)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(frames, intr, seconds=max(2.0, args.cpu_seconds / 4))
+        if i >= args.warmup:
+            vals.append(cb)
+    v = statistics.median(c["value"] for c in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpixel/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "bounded row bands of frame 0 per step"},
+            "cpu_baseline": {"value": v, "unit": "Mpixel/s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    import paper_1707_00385_gb300 as pc
+    from paper_1707_00385_gb300 import build as pcbuild
+    pcbuild.build()
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    nsc = max(1, min(args.scenes, args.frames))
+    sc = scenes(nsc)
+    intr = sc[0].intrinsics
+    F = args.frames
+    host = [sc[i % nsc].depth for i in range(F)]
+    flop_frame = [counted_flop(s.depth) for s in sc]
+    flop_step = sum(flop_frame[i % nsc] for i in range(F))
+    depth = [torch.from_numpy(h).to(dev) for h in host]          # F distinct buffers
+    k1 = [torch.empty((H, W), device=dev) for _ in range(F)]
+    k2 = [torch.empty((H, W), device=dev) for _ in range(F)]
+    nrm = [torch.empty((H, W, 3), device=dev) for _ in range(F)]
+    curv = pc.Curvature(*intr, window_radius=RADIUS, iterations=ITERS)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        for i in range(F):
+            curv(depth[i], k1[i], k2[i], nrm[i], stream=stream)
+
+    # ---- device-timed region: inputs resident in HBM
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    ms_step = ms / args.steps
+    px_total = float(world) * args.steps * F * H * W
+    value = px_total / (ms / 1e3) / 1e6
+    launch_ms = ms_step / F   # one kernel per frame, launched back to back
+    clocks = clk.summary()
+
+    # ---- end to end through the host-memory entry point (pinned buffers)
+    hd = [torch.from_numpy(h).pin_memory() for h in host]
+    hk1 = [torch.empty((H, W)).pin_memory() for _ in range(F)]
+    hk2 = [torch.empty((H, W)).pin_memory() for _ in range(F)]
+    hn = [torch.empty((H, W, 3)).pin_memory() for _ in range(F)]
+    e2e_ctx = pc.Curvature(*intr, window_radius=RADIUS, iterations=ITERS)
+
+    def step_host():
+        for i in range(F):
+            e2e_ctx.compute_host(hd[i], hk1[i], hk2[i], hn[i], stream=stream)
+        stream.synchronize()
+
+    for _ in range(max(1, args.warmup)):
+        step_host()
+    barrier()
+    e2e_steps = max(2, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_host()
+    t1 = time.perf_counter()
+    barrier()
+    e2e_s = max_over_ranks(t1 - t0)
+    e2e_val = float(world) * e2e_steps * F * H * W / e2e_s / 1e6
+    # results of both paths agree (same kernel, same inputs)
+    same = bool(torch.equal(hk1[0], k1[0].cpu()) or np.array_equal(hk1[0].numpy(), k1[0].cpu().numpy(),
+                                                                  equal_nan=True))
+
+    # ---- roofline of the fused kernel: counted FP32 work vs the FP32 ALU peak
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = (flop_step / F) / (launch_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": recorded_traffic(),
+            "kernel": "k_fit<7> (fused normal + IRLS + eigen), one launch per 640x480 frame",
+            "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                          f"{sm_max:.0f} MHz max SM clock (derived)",
+            "launch_ms": launch_ms, "counted_flop_per_launch": flop_step / F}
+
+    line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "H": H, "W": W, "window_radius": RADIUS, "iterations": ITERS,
+                       "frames_per_step": F, "distinct_scenes": nsc,
+                       "l2": (f"inputs larger than L2: {F} distinct frame buffers "
+                              f"({F * H * W * 4 / 1e6:.0f} MB of ranges) per step"
+                              if F * H * W * 4 > 129e6 else
+                              f"inputs smaller than L2 ({F * H * W * 4 / 1e6:.0f} MB): profiling case only"),
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_val, "unit": "Mpixel/s", "h2d_bytes_per_step": F * H * W * 4,
+                    "d2h_bytes_per_step": F * H * W * 4 * 5, "api": "pc_compute_host",
+                    "matches_device_path": same},
+            "gpu_launches": args.steps * F,
+            "clocks": clocks,
+            "roofline": roof}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline([s.depth for s in sc], intr, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    curv.close()
+    e2e_ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

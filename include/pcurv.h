@@ -1,0 +1,128 @@
+/*
+ * pcurv.h -- C ABI of the GB300 (sm_103a) principal-curvature library.
+ *
+ * Method: Spek, Li, Drummond, "A Fast Method For Computing Principal
+ * Curvatures From Range Images" (arXiv 1707.00385).  For every pixel of a
+ * range image the library
+ *   - back-projects the window around it through the pinhole intrinsics
+ *     (Sec. 3.2, first pipeline item), relative to the pixel's own point
+ *     (p'_i = p_i - p, Sec. 3.1.2);
+ *   - estimates an initial normal by regressing z on x and y over a
+ *     (2*normal_radius+1)^2 patch (Sec. 3.2.1, Eq. initialnormal);
+ *   - fits the parabolic patch z = A/2 x^2 + B x y + C/2 y^2 in a frame
+ *     rotated by (theta_x, theta_y) and offset by t_z (Sec. 3.1.2, Eq. quad),
+ *     by `iterations` re-weighted Gauss-Newton steps with weights
+ *     W(eps) = k / (k + eps^2) (Sec. 3.2.3, Eqs. iter_reweighted_update and
+ *     weighting_function);
+ *   - returns k1 = T1 + T2 >= k2 = T1 - T2, T1 = (A + C)/2,
+ *     T2 = sqrt(T1^2 - AC + B^2) (Sec. 3.1.2), and the refined normal, the
+ *     local z axis of the final frame (Sec. 3.2.4).
+ *
+ * Conventions
+ *   - Range images are float32, row major, H rows by W columns, in metres;
+ *     pixel (u, v) is column u, row v, with its centre at integer (u, v).
+ *     A range that is not finite or not > 0 marks "no measurement".
+ *   - Curvatures are in 1/metre; a surface convex towards the camera is
+ *     positive (a sphere of radius rho gives 1/rho, 1/rho).  Normals are unit
+ *     vectors in the camera frame pointing away from the camera, stored as
+ *     H*W*3 interleaved floats (n_x, n_y, n_z per pixel).
+ *   - A pixel without a result (no range, degenerate normal patch, fewer than
+ *     min_window valid window points, or a singular re-weighted system)
+ *     gets quiet NaN in k1, k2 and all three normal components.
+ *   - Device pointers are caller-owned CUDA device memory (cudaMalloc or
+ *     managed), 4-byte aligned, with no overlap between inputs and outputs.
+ *     Host pointers are caller-owned host memory; page-locked memory lets the
+ *     copies run asynchronously.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Compute calls only enqueue work: they return once the work is
+ *     queued; the caller synchronises the stream before reading results.
+ *   - Arguments are checked before anything is enqueued; a call that returns
+ *     an error has enqueued nothing, except PC_ERR_CUDA from a failed launch
+ *     or copy (pc_last_error() then holds the CUDA message).
+ *   - A context is not thread safe: use one per host thread.  No C++
+ *     exception crosses this interface.
+ */
+#ifndef PCURV_H
+#define PCURV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pc_ctx pc_ctx; /* opaque; owns parameters and staging buffers */
+
+typedef enum pc_status {
+    PC_OK = 0,
+    PC_ERR_INVALID_ARG = 1, /* NULL/misaligned/host pointer, size or parameter out of range */
+    PC_ERR_CUDA = 2,        /* a CUDA call failed; see pc_last_error() */
+    PC_ERR_OOM = 3,         /* device or host allocation failed */
+    PC_ERR_TIMEOUT = 4,     /* reserved: a bounded device wait gave up */
+    PC_ERR_UNSUPPORTED = 5  /* parameter combination this build does not implement */
+} pc_status;
+
+/* Limits checked by every call. */
+#define PC_MAX_RADIUS 24         /* window radius r: (2r+1)^2 points */
+#define PC_MAX_NORMAL_RADIUS 8   /* initial-normal patch radius */
+#define PC_MAX_ITERATIONS 64     /* re-weighted iterations */
+#define PC_MAX_DIM 16384         /* H and W */
+
+/* Tunable parameters of the method.  Fill with pc_params_default() first. */
+typedef struct pc_params {
+    float k;             /* constant k of W(eps) = k/(k+eps^2), m^2 (Sec. 3.2.3). Default 1e-4 */
+    int reject;          /* 1 = rejection filter: W = 0 unless eps^2 <= reject_ratio * MSE of the
+                            window at the same iteration (Sec. 3.2.3). Default 0 */
+    float reject_ratio;  /* default 2 ("twice the mean squared error", Sec. 3.2.3) */
+    int normal_radius;   /* initial-normal patch radius; 3 gives the 7x7 patch of Sec. 3.2.1 */
+    int stride;          /* window sampling stride (1 = dense; >1 samples the (2r+1)^2
+                            square sparsely, as the 37x37 patch of Sec. 4.2.1). Default 1 */
+    float det_tol;       /* normal patch degenerate when det M <= det_tol * (tr M)^2. Default 1e-6 */
+    float pivot_tol;     /* re-weighted system singular when a pivot of the Jacobi-scaled
+                            Cholesky factorisation is <= pivot_tol (a scaled condition estimate
+                            above 1/pivot_tol).  Default 1e-5: single-precision moment sums
+                            carry ~1e-6 relative error, so smaller pivots are not resolved */
+    int min_window;      /* fewest valid window points accepted. Default 6 */
+} pc_params;
+
+/* Writes the defaults above into *p (no-op for NULL). */
+void pc_params_default(pc_params* p);
+
+/* Creates a context for camera intrinsics fx, fy, cx, cy (pixels; fx, fy > 0,
+ * all finite), window radius 1..PC_MAX_RADIUS, iterations 0..PC_MAX_ITERATIONS
+ * and params (NULL = defaults).  Host only: touches no GPU.  On success *out
+ * receives the context; on error *out is set to NULL. */
+pc_status pc_create(float fx, float fy, float cx, float cy, int window_radius, int iterations,
+                    const pc_params* params, pc_ctx** out);
+
+/* Principal curvatures of one range image (the whole pipeline of Sec. 3.2).
+ *   depth      device, H*W floats (read only)
+ *   k1_out     device, H*W floats: larger principal curvature, 1/m
+ *   k2_out     device, H*W floats: smaller principal curvature, 1/m
+ *   normal_out device, H*W*3 floats, or NULL to skip the refined normals
+ * H == 0 or W == 0 is a valid empty image (PC_OK, nothing enqueued). */
+pc_status pc_compute(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* k1_out,
+                     float* k2_out, float* normal_out);
+
+/* The same from and to HOST buffers: copies depth to device staging buffers
+ * owned by ctx, computes, and copies k1, k2 (and normal when not NULL) back,
+ * all enqueued on `stream`.  The host buffers must stay valid until the
+ * stream is synchronised.  Staging buffers are (re)allocated on the current
+ * device when a larger image arrives (PC_ERR_OOM if that fails); successive
+ * calls on one ctx must use one stream, or synchronise in between. */
+pc_status pc_compute_host(pc_ctx* ctx, const float* depth_host, int H, int W, void* stream,
+                          float* k1_host, float* k2_host, float* normal_host);
+
+/* Frees the context and its staging buffers (synchronising the device first
+ * when it owns any).  NULL is a no-op returning PC_OK. */
+pc_status pc_destroy(pc_ctx* ctx);
+
+/* Static description of a status code. */
+const char* pc_status_string(pc_status s);
+
+/* Message of the last failing CUDA call seen by ctx ("" if none; ctx may be NULL). */
+const char* pc_last_error(const pc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCURV_H */

@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) per-pixel principal curvature from range images.
+
+Implements the iterative quadric-patch fit of Spek, Li and Drummond, "A Fast
+Method For Computing Principal Curvatures From Range Images" (arXiv
+1707.00385) as hand-written CUDA kernels behind the C ABI in include/pcurv.h.
+This package holds the kernels (csrc/), their build (build.py) and the
+ctypes binding (pcurv.py).
+"""
+from .pcurv import (  # noqa: F401
+    PC_OK, PC_ERR_INVALID_ARG, PC_ERR_CUDA, PC_ERR_OOM, PC_ERR_TIMEOUT, PC_ERR_UNSUPPORTED,
+    Curvature, PcError, load, pc_compute, pc_compute_host, pc_create, pc_destroy, pc_last_error,
+    pc_params, pc_params_default, pc_status_string,
+)

@@ -1,0 +1,178 @@
+"""Python binding of the C ABI in include/pcurv.h (ctypes; argument marshalling only).
+
+The functions keep the C names (pc_create, pc_compute, pc_compute_host,
+pc_destroy, pc_status_string, pc_params_default, pc_last_error) and take raw
+addresses.  `Curvature` wraps them for torch tensors: torch supplies device
+memory and the CUDA stream, every step of the method runs in the library's
+kernels.  There is no fallback: if libpcurv.so is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libpcurv.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pcurv.h")
+
+PC_OK, PC_ERR_INVALID_ARG, PC_ERR_CUDA, PC_ERR_OOM, PC_ERR_TIMEOUT, PC_ERR_UNSUPPORTED = range(6)
+PC_MAX_RADIUS, PC_MAX_NORMAL_RADIUS, PC_MAX_ITERATIONS, PC_MAX_DIM = 24, 8, 64, 16384
+
+
+class pc_params(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_float),
+        ("reject", ctypes.c_int),
+        ("reject_ratio", ctypes.c_float),
+        ("normal_radius", ctypes.c_int),
+        ("stride", ctypes.c_int),
+        ("det_tol", ctypes.c_float),
+        ("pivot_tol", ctypes.c_float),
+        ("min_window", ctypes.c_int),
+    ]
+
+
+class PcError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        msg = f"{what}: {pc_status_string(status)} ({status})"
+        super().__init__(msg + (f": {detail}" if detail else ""))
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def load() -> ctypes.CDLL:
+    """Loads libpcurv.so (built by __graft_entry__.build() or
+    `python -m paper_1707_00385_gb300.build`)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.pc_params_default.argtypes = [ctypes.POINTER(pc_params)]
+        L.pc_params_default.restype = None
+        L.pc_create.argtypes = [ctypes.c_float] * 4 + [ctypes.c_int, ctypes.c_int,
+                                                       ctypes.POINTER(pc_params), ctypes.POINTER(_vp)]
+        L.pc_compute.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.pc_compute_host.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.pc_destroy.argtypes = [_vp]
+        L.pc_status_string.argtypes = [ctypes.c_int]
+        L.pc_status_string.restype = ctypes.c_char_p
+        L.pc_last_error.argtypes = [_vp]
+        L.pc_last_error.restype = ctypes.c_char_p
+        for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_destroy"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+# ---- the C functions, same names --------------------------------------------
+
+def pc_params_default() -> pc_params:
+    p = pc_params()
+    load().pc_params_default(ctypes.byref(p))
+    return p
+
+
+def pc_create(fx, fy, cx, cy, window_radius, iterations, params: pc_params | None = None):
+    """Returns (status, ctx handle or None)."""
+    out = _vp()
+    st = load().pc_create(fx, fy, cx, cy, window_radius, iterations,
+                          ctypes.byref(params) if params is not None else None, ctypes.byref(out))
+    return st, (out.value if st == PC_OK else None)
+
+
+def pc_compute(ctx, depth, H, W, stream, k1_out, k2_out, normal_out) -> int:
+    return load().pc_compute(ctx, depth, H, W, stream, k1_out, k2_out, normal_out)
+
+
+def pc_compute_host(ctx, depth_host, H, W, stream, k1_host, k2_host, normal_host) -> int:
+    return load().pc_compute_host(ctx, depth_host, H, W, stream, k1_host, k2_host, normal_host)
+
+
+def pc_destroy(ctx) -> int:
+    return load().pc_destroy(ctx)
+
+
+def pc_status_string(status: int) -> str:
+    return load().pc_status_string(status).decode()
+
+
+def pc_last_error(ctx) -> str:
+    return load().pc_last_error(ctx).decode()
+
+
+# ---- torch convenience wrapper ----------------------------------------------
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Curvature:
+    """A pc_ctx for one camera and one parameter set.
+
+    c = Curvature(fx, fy, cx, cy, window_radius=7, iterations=5)
+    k1, k2, normal = c(depth)          # depth: CUDA float32 H x W tensor
+    """
+
+    def __init__(self, fx, fy, cx, cy, window_radius=7, iterations=5, **params):
+        p = pc_params_default()
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        st, ctx = pc_create(fx, fy, cx, cy, window_radius, iterations, p)
+        if st != PC_OK:
+            raise PcError(st, "pc_create")
+        self.ctx = ctx
+        self.params = p
+        self.window_radius, self.iterations = window_radius, iterations
+
+    def close(self):
+        if self.ctx is not None:
+            pc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __call__(self, depth, k1=None, k2=None, normal=None, want_normal=True, stream=None):
+        """Enqueues the method on `stream` (default: torch's current stream)
+        and returns (k1, k2, normal); normal is None when want_normal is False."""
+        import torch
+        if depth.dtype != torch.float32 or not depth.is_cuda or depth.dim() != 2:
+            raise ValueError("depth must be a 2-D float32 CUDA tensor")
+        depth = depth.contiguous()
+        H, W = depth.shape
+        if k1 is None:
+            k1 = torch.empty((H, W), dtype=torch.float32, device=depth.device)
+        if k2 is None:
+            k2 = torch.empty((H, W), dtype=torch.float32, device=depth.device)
+        if want_normal and normal is None:
+            normal = torch.empty((H, W, 3), dtype=torch.float32, device=depth.device)
+        for t in (k1, k2) + ((normal,) if normal is not None else ()):
+            if not t.is_contiguous() or t.dtype != torch.float32:
+                raise ValueError("outputs must be contiguous float32")
+        st = pc_compute(self.ctx, depth.data_ptr(), H, W, _stream_handle(stream), k1.data_ptr(),
+                        k2.data_ptr(), normal.data_ptr() if normal is not None else None)
+        if st != PC_OK:
+            raise PcError(st, "pc_compute", pc_last_error(self.ctx))
+        return k1, k2, normal
+
+    def compute_host(self, depth, k1, k2, normal=None, stream=None):
+        """Host-memory form (pc_compute_host): depth, k1, k2, normal are CPU
+        float32 tensors (pinned for asynchronous copies).  Enqueues the copies
+        and the kernel; synchronise the stream before reading the outputs."""
+        H, W = depth.shape
+        st = pc_compute_host(self.ctx, depth.data_ptr(), H, W, _stream_handle(stream), k1.data_ptr(),
+                             k2.data_ptr(), normal.data_ptr() if normal is not None else None)
+        if st != PC_OK:
+            raise PcError(st, "pc_compute_host", pc_last_error(self.ctx))

@@ -1,0 +1,121 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every function
+include/pcurv.h declares, and rejects bad arguments before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pcurv.h")
+
+
+@pytest.fixture(scope="module")
+def pc():
+    from paper_1707_00385_gb300 import build
+    build.build()
+    import paper_1707_00385_gb300 as pc
+    pc.load()
+    return pc
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pc_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_destroy", "pc_status_string",
+              "pc_params_default", "pc_last_error"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(pc):
+    lib = ctypes.CDLL(pc.pcurv.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_params_struct_matches_header(pc):
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct pc_params \{(.*?)\} pc_params;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(float|int)\s+(\w+);", body)
+    assert [f for _, f in fields] == [f for f, _ in pc.pc_params._fields_]
+    ctype = {"float": ctypes.c_float, "int": ctypes.c_int}
+    assert all(ctype[t] is c for (t, _), (_, c) in zip(fields, pc.pc_params._fields_))
+
+
+def test_limits_match_header(pc):
+    text = open(HEADER).read()
+    for name in ("PC_MAX_RADIUS", "PC_MAX_NORMAL_RADIUS", "PC_MAX_ITERATIONS", "PC_MAX_DIM"):
+        val = int(re.search(rf"#define {name} (\d+)", text).group(1))
+        assert getattr(pc.pcurv, name) == val
+
+
+def test_defaults(pc):
+    p = pc.pc_params_default()
+    assert p.k == pytest.approx(1e-4) and p.reject == 0 and p.reject_ratio == 2.0
+    assert p.normal_radius == 3 and p.stride == 1 and p.min_window == 6
+    assert p.pivot_tol == pytest.approx(1e-5) and p.det_tol == pytest.approx(1e-6)
+
+
+def test_status_strings(pc):
+    for s in range(6):
+        assert pc.pc_status_string(s) and pc.pc_status_string(s) != "unknown status"
+    assert pc.pc_status_string(99) == "unknown status"
+
+
+@pytest.mark.parametrize("args", [
+    (0.0, 525.0, 319.5, 239.5, 7, 5), (525.0, -1.0, 319.5, 239.5, 7, 5),
+    (float("nan"), 525.0, 319.5, 239.5, 7, 5), (525.0, 525.0, float("inf"), 239.5, 7, 5),
+    (525.0, 525.0, 319.5, 239.5, 0, 5), (525.0, 525.0, 319.5, 239.5, 25, 5),
+    (525.0, 525.0, 319.5, 239.5, 7, -1), (525.0, 525.0, 319.5, 239.5, 7, 65),
+])
+def test_create_rejects_bad_arguments(pc, args):
+    st, ctx = pc.pc_create(*args)
+    assert st == pc.PC_ERR_INVALID_ARG and ctx is None
+
+
+@pytest.mark.parametrize("field,value", [("k", 0.0), ("k", float("nan")), ("reject", 2),
+                                         ("reject_ratio", 0.0), ("normal_radius", 0),
+                                         ("normal_radius", 9), ("stride", 0), ("min_window", 5),
+                                         ("pivot_tol", -1.0), ("det_tol", float("inf"))])
+def test_create_rejects_bad_params(pc, field, value):
+    p = pc.pc_params_default()
+    setattr(p, field, value)
+    st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5, p)
+    assert st == pc.PC_ERR_INVALID_ARG and ctx is None
+
+
+def test_compute_argument_checks_without_gpu(pc):
+    st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5)
+    assert st == pc.PC_OK
+    try:
+        assert pc.pc_compute(None, None, 10, 10, None, None, None, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute(ctx, None, -1, 10, None, None, None, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute(ctx, None, 10, 16385, None, None, None, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute(ctx, None, 0, 10, None, None, None, None) == pc.PC_OK    # empty image
+        assert pc.pc_compute(ctx, None, 10, 0, None, None, None, None) == pc.PC_OK
+        assert pc.pc_compute(ctx, None, 10, 10, None, None, None, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute_host(ctx, None, 10, 10, None, None, None, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute_host(ctx, None, 0, 0, None, None, None, None) == pc.PC_OK
+        # a misaligned pointer is rejected before any CUDA call
+        buf = (ctypes.c_float * 64)()
+        addr = ctypes.addressof(buf)
+        assert pc.pc_compute(ctx, addr + 2, 4, 4, None, addr, addr, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_last_error(ctx) == ""
+    finally:
+        assert pc.pc_destroy(ctx) == pc.PC_OK
+    assert pc.pc_destroy(None) == pc.PC_OK
+    assert pc.pc_last_error(None) == ""
+
+
+def test_binding_fails_loudly_without_library(pc, monkeypatch, tmp_path):
+    import paper_1707_00385_gb300.pcurv as b
+    monkeypatch.setattr(b, "_lib", None)
+    monkeypatch.setattr(b, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        b.load()

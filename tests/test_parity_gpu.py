@@ -1,0 +1,138 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element,
+on seeded synthetic range images.
+
+Rule (oracle/parity.py): |dk| <= 1e-4 + 1e-4 |k| for k1 and k2 on every
+well-posed pixel (the oracle's own answer is fixed to a quarter of that
+tolerance under single-precision-sized perturbation); validity agrees except
+at the singularity threshold; NaN patterns of k1, k2 and the normal agree.
+Each case also has a floor on the well-posed fraction and on the fraction of
+all pixels within tolerance, so a regression cannot hide behind the rule."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+PIVOT_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_00385_gb300 import build
+    build.build()
+    import paper_1707_00385_gb300 as pc
+    pc.load()
+    return pc
+
+
+def run_gpu(pc, depth, intr, r, T, **params):
+    import torch
+    c = pc.Curvature(*intr, window_radius=r, iterations=T, **params)
+    d = torch.from_numpy(np.ascontiguousarray(depth, dtype=np.float32)).cuda()
+    k1, k2, n = c(d)
+    torch.cuda.synchronize()
+    out = k1.cpu().numpy(), k2.cpu().numpy(), n.cpu().numpy()
+    c.close()
+    return out
+
+
+def check(pc, orc, scene, r, T, min_well_posed, min_within, uv=None, **params):
+    from oracle import parity
+    k1, k2, n = run_gpu(pc, scene.depth, scene.intrinsics, r, T, **params)
+    p = orc.params(*scene.intrinsics, r=r, T=T, pivot_tol=PIVOT_TOL, **params)
+    ref = parity.reference(scene.depth, p, nthreads=0, uv=uv)
+    if uv is not None:
+        k1, k2, n = k1[uv[:, 1], uv[:, 0]], k2[uv[:, 1], uv[:, 0]], n[uv[:, 1], uv[:, 0]]
+    rep = parity.compare(k1, k2, n, ref, pivot_tol=PIVOT_TOL)
+    print(rep.summary())
+    assert rep.nan_pattern_ok
+    assert rep.n_validity_mismatch == 0, rep.summary()
+    assert rep.n_well_posed_bad == 0, rep.summary()
+    assert rep.n_well_posed >= min_well_posed * rep.n_valid_oracle, rep.summary()
+    assert rep.frac_within_tol_all >= min_within, rep.summary()
+    assert rep.max_normal_angle_well_posed < 1e-4, rep.summary()
+    return rep
+
+
+@pytest.fixture(scope="module")
+def kinect640():
+    return synth.kinect_scene(0)
+
+
+@pytest.fixture(scope="module")
+def crop(kinect640):
+    # 70 x 100: several 32 x 8 tiles and a ragged tail in both directions
+    return synth.crop(kinect640, 180, 250, 70, 100)
+
+
+def test_sphere_scene_64x48(gpu, orc):
+    """64 x 48 sphere (r = 0.10 m at 0.80 m) in front of a plane, 1 mm noise,
+    window radius 3, 3 iterations, whole image."""
+    check(gpu, orc, synth.sphere_scene(0), 3, 3, min_well_posed=0.85, min_within=0.9)
+
+
+@pytest.mark.parametrize("r", [3, 7, 11])
+def test_kinect_crop_radii(gpu, orc, crop, r):
+    check(gpu, orc, crop, r, 5, min_well_posed=0.5, min_within=0.8)
+
+
+def test_kinect_crop_sparse_window(gpu, orc, crop):
+    """Strided window (run-time radius path): 15 x 15 sampled every 2 pixels."""
+    check(gpu, orc, crop, 7, 5, min_well_posed=0.5, min_within=0.8, stride=2)
+
+
+def test_kinect_crop_runtime_radius(gpu, orc, crop):
+    """Radius 15, beyond the unrolled instantiations."""
+    check(gpu, orc, crop, 15, 3, min_well_posed=0.4, min_within=0.7)
+
+
+def test_kinect_crop_rejection(gpu, orc, crop):
+    """The rejection filter of the weighting function (weight 0 above 2 MSE)."""
+    check(gpu, orc, crop, 7, 5, min_well_posed=0.5, min_within=0.8, reject=1)
+
+
+def test_kinect_crop_other_k_and_normal_radius(gpu, orc, crop):
+    check(gpu, orc, crop, 5, 4, min_well_posed=0.5, min_within=0.8, k=4e-4, normal_radius=2)
+
+
+def test_full_frame_sampled(gpu, orc, kinect640):
+    """640 x 480, radius 7, 5 iterations (the benchmark's launch): 2500 random
+    pixels plus two whole 32 x 8 tiles (a corner and an interior one)."""
+    rng = np.random.default_rng(7)
+    uv = np.stack([rng.integers(0, 640, 2500), rng.integers(0, 480, 2500)], 1)
+    tiles = [np.stack(np.meshgrid(np.arange(u0, u0 + 32), np.arange(v0, v0 + 8)), -1).reshape(-1, 2)
+             for u0, v0 in ((0, 0), (320, 240))]
+    uv = np.concatenate([uv] + tiles).astype(np.int32)
+    check(gpu, orc, kinect640, 7, 5, min_well_posed=0.6, min_within=0.85, uv=uv)
+
+
+def test_tof_scene_512x424(gpu, orc):
+    """Time-of-flight noise model at 512 x 424 (sampled pixels)."""
+    s = synth.kinect_scene(3, H=424, W=512, noise="tof")
+    rng = np.random.default_rng(3)
+    uv = np.stack([rng.integers(0, 512, 1500), rng.integers(0, 424, 1500)], 1).astype(np.int32)
+    check(gpu, orc, s, 7, 5, min_well_posed=0.6, min_within=0.85, uv=uv)
+
+
+def test_noise_free_scene_all_pixels_close(gpu, orc):
+    """Without noise almost every pixel converges and must match."""
+    s = synth.crop(synth.kinect_scene(1, noise="none", invalid_frac=0.0), 200, 200, 48, 80)
+    check(gpu, orc, s, 7, 5, min_well_posed=0.8, min_within=0.9)
+
+
+def test_closed_form_paraboloid_on_gpu(gpu):
+    """A paraboloid z = z0 + a X^2 + c Y^2 seen along its axis: (2a, 2c) at the
+    apex (float32 ranges, so to a few 1e-4 relative)."""
+    cam = synth.Camera(31, 31, 300.0, 300.0, 15.0, 15.0)
+    rays = cam.rays()
+    a, c, z0 = 3.0, -5.0, 1.2
+    q = a * rays[..., 0] ** 2 + c * rays[..., 1] ** 2
+    depth = (2 * z0 / (1 + np.sqrt(1 - 4 * q * z0))).astype(np.float32)
+    k1, k2, n = run_gpu(gpu, depth, (300.0, 300.0, 15.0, 15.0), 7, 4)
+    assert k1[15, 15] == pytest.approx(6.0, rel=2e-3)
+    assert k2[15, 15] == pytest.approx(-10.0, rel=2e-3)
+    assert np.allclose(n[15, 15], [0, 0, 1], atol=1e-5)
