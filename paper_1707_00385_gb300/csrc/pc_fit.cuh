@@ -2,10 +2,11 @@
 //
 // One CTA computes a 32 x 8 tile of output pixels, one thread per pixel.  The
 // CTA first stages the tile's range values plus a halo of max(r, r_n) pixels
-// into shared memory as (Z, c) pairs, c = 1 for a valid range and +inf for
-// none (outside the image, zero, negative or not finite).  Each thread then
-// runs the whole method of Spek, Li and Drummond (arXiv 1707.00385, Sec. 3.2)
-// for its pixel in registers:
+// into shared memory as two planes, Z and c, c = 1 for a valid range and +inf
+// for none (outside the image, zero, negative or not finite), and counts the
+// valid window points of every pixel row by row.  Each thread then runs the
+// whole method of Spek, Li and Drummond (arXiv 1707.00385, Sec. 3.2) for its
+// pixel in registers:
 //
 //   initial normal   Sec. 3.2.1, Eq. initialnormal (7x7 regression)
 //   frame            Sec. 3.2.2 (minimal rotation to the normal, A=B=C=t_z=0)
@@ -31,11 +32,29 @@
 //     sums, because with j = (j0, j1, -1, x^2/2, x y, y^2/2) the (A,B,C)
 //     block only has five distinct moments (H_AC and H_BB share x^2 y^2) and
 //     the t_z row is sums of w j.
+//   * window points are visited in pairs, p'(du, dv) with p'(-du, -dv), in
+//     packed FP32x2 instructions (pc_f32x2.cuh): both points share every
+//     per-iteration coefficient, their alpha coefficients are exact negatives
+//     of each other, so one instruction does the work of two and each sum is
+//     kept as a pair of partial sums, added once per iteration.  The centre
+//     point (p' = 0) contributes only to sum w and sum w eps.
 #pragma once
 #include <cfloat>
 #include <cuda_runtime.h>
 
+#include "pc_f32x2.cuh"
 #include "pc_internal.h"
+
+// Column unroll factor of the window loops of the fixed-radius kernels
+// (0 = unroll the whole row) and the CTAs per SM the register budget targets.
+#ifndef PC_COL_UNROLL
+#define PC_COL_UNROLL 0
+#endif
+#ifndef PC_MIN_BLOCKS
+#define PC_MIN_BLOCKS 2
+#endif
+#define PC_STR(x) #x
+#define PC_UNROLL(n) _Pragma(PC_STR(unroll n))
 
 namespace pcurv {
 
@@ -48,115 +67,139 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fffffff); }
 
-// 26 running sums of one iteration (see the header comment).
-struct Moments {
-    float h00, h01, h11;       // sum w j0 j0, w j0 j1, w j1 j1
-    float s0, s1;              // sum w j0, w j1           (t_z column, times -1)
-    float h03, h04, h05;       // sum w j0 x^2, w j0 x y, w j0 y^2
-    float h13, h14, h15;       // sum w j1 x^2, w j1 x y, w j1 y^2
-    float sw;                  // sum w                    (t_z, t_z)
-    float sxx, sxy, syy;       // sum w x^2, w x y, w y^2  (t_z row, times -1)
-    float m40, m31, m22, m13, m04;  // sum w x^4, w x^3 y, w x^2 y^2, w x y^3, w y^4
-    float g0, g1, ge, g3, g4, g5;   // sum w eps j0, w eps j1, w eps, w eps x^2, w eps x y, w eps y^2
+// 26 running sums of one iteration, each as a pair of partial sums (the two
+// points of a symmetric pair).  j0 is carried negated (nj0 = -j0).
+struct Moments2 {
+    f32x2 h00, h01, h11;       // sum w j0 j0, -w j0 j1, w j1 j1
+    f32x2 s0, s1;              // sum -w j0, w j1
+    f32x2 h03, h04, h05;       // sum -w j0 x^2, -w j0 x y, -w j0 y^2
+    f32x2 h13, h14, h15;       // sum w j1 x^2, w j1 x y, w j1 y^2
+    f32x2 sw;                  // sum w
+    f32x2 sxx, sxy, syy;       // sum w x^2, w x y, w y^2
+    f32x2 m40, m31, m22, m13, m04;  // sum w x^4, w x^3 y, w x^2 y^2, w x y^3, w y^4
+    f32x2 g0, g1, ge, g3, g4, g5;   // sum -w eps j0, w eps j1, w eps, w eps x^2, w eps x y, w eps y^2
 };
 
-// Per-iteration constants of one pixel.
-struct Coef {
-    float cx0, cy0, bx;   // x = Z (du cx0 + dv cy0) + dZ bx
-    float cx1, cy1, by;   // y
-    float cx2, cy2, bh;   // h (local z before the offset t_z)
-    float hA, hC;         // A/2, C/2
-    float A, B, C, tz;
-    float invk, Zp;
+// Per-iteration constants of one pixel, splat into pairs.
+struct Coef2 {
+    f32x2 cx0, cx1, cx2;       // x = Z (du cx0 + dv cy0) + dZ bx, likewise y, h
+    f32x2 bx, by, bh;
+    f32x2 hA, hC, A, B, C;     // A/2, C/2, A, B, C
+    f32x2 ntz;                 // -t_z
+    f32x2 invk;                // 1/k
+    f32x2 nzp;                 // -Z_p
 };
 
-__device__ __forceinline__ void zero(Moments& m) {
-    m.h00 = m.h01 = m.h11 = m.s0 = m.s1 = 0.f;
-    m.h03 = m.h04 = m.h05 = m.h13 = m.h14 = m.h15 = 0.f;
-    m.sw = m.sxx = m.sxy = m.syy = 0.f;
-    m.m40 = m.m31 = m.m22 = m.m13 = m.m04 = 0.f;
-    m.g0 = m.g1 = m.ge = m.g3 = m.g4 = m.g5 = 0.f;
+__device__ __forceinline__ void zero(Moments2& m) {
+    const f32x2 z = 0ull;
+    m.h00 = m.h01 = m.h11 = m.s0 = m.s1 = z;
+    m.h03 = m.h04 = m.h05 = m.h13 = m.h14 = m.h15 = z;
+    m.sw = m.sxx = m.sxy = m.syy = z;
+    m.m40 = m.m31 = m.m22 = m.m13 = m.m04 = z;
+    m.g0 = m.g1 = m.ge = m.g3 = m.g4 = m.g5 = z;
 }
 
-// Local coordinates (x, y, h) of one window point.
-__device__ __forceinline__ void local_xyz(const Coef& k, float Z, float du, float rx, float ry,
-                                          float rh, float& x, float& y, float& h) {
-    const float dZ = Z - k.Zp;
-    x = fmaf(fmaf(du, k.cx0, rx), Z, k.bx * dZ);
-    y = fmaf(fmaf(du, k.cx1, ry), Z, k.by * dZ);
-    h = fmaf(fmaf(du, k.cx2, rh), Z, k.bh * dZ);
+// Local coordinates (x, y, h) of a pair.  DU = (du, -du); RX = (dv cy0, -dv cy0).
+__device__ __forceinline__ void local_xyz2(const Coef2& k, f32x2 Z, f32x2 DU, f32x2 RX, f32x2 RY,
+                                           f32x2 RH, f32x2& X, f32x2& Y, f32x2& Hh) {
+    const f32x2 dZ = add2(Z, k.nzp);
+    X = fma2(fma2(DU, k.cx0, RX), Z, mul2(k.bx, dZ));
+    Y = fma2(fma2(DU, k.cx1, RY), Z, mul2(k.by, dZ));
+    Hh = fma2(fma2(DU, k.cx2, RH), Z, mul2(k.bh, dZ));
 }
 
-// One point visit: residual (Eq. quad in the local frame), weight, Jacobian,
-// and the 26 sums.  c = 1 for a valid point, +inf for none.
+// One symmetric pair: residuals (Eq. quad in the local frame), weights,
+// Jacobian rows and the 26 sums.  C = (c_a, c_b), 1 valid / +inf invalid.
 template <bool REJECT>
-__device__ __forceinline__ void visit(Moments& m, const Coef& k, float Z, float c, float du,
-                                      float rx, float ry, float rh, float thr) {
-    float x, y, h;
-    local_xyz(k, Z, du, rx, ry, rh, x, y, h);
-    const float xx = x * x, xy = x * y, yy = y * y;
-    // eps = A/2 x^2 + B x y + C/2 y^2 - (h + t_z)
-    const float eps = fmaf(k.hA, xx, fmaf(k.B, xy, fmaf(k.hC, yy, -(h + k.tz))));
-    const float e2 = eps * eps;
-    float w = rcp_approx(fmaf(e2, k.invk, c));
-    if (REJECT) w = (e2 <= thr) ? w : 0.f;
-    // d eps / d theta_x = -(B x + C y) h - y ; d eps / d theta_y = (A x + B y) h + x
-    const float j0 = fmaf(-fmaf(k.B, x, k.C * y), h, -y);
-    const float j1 = fmaf(fmaf(k.A, x, k.B * y), h, x);
-    const float we = w * eps;
-    const float wj0 = w * j0, wj1 = w * j1;
-    const float wxx = w * xx, wxy = w * xy, wyy = w * yy;
-    m.h00 = fmaf(wj0, j0, m.h00);
-    m.h01 = fmaf(wj0, j1, m.h01);
-    m.h11 = fmaf(wj1, j1, m.h11);
-    m.s0 += wj0;
-    m.s1 += wj1;
-    m.h03 = fmaf(wj0, xx, m.h03);
-    m.h04 = fmaf(wj0, xy, m.h04);
-    m.h05 = fmaf(wj0, yy, m.h05);
-    m.h13 = fmaf(wj1, xx, m.h13);
-    m.h14 = fmaf(wj1, xy, m.h14);
-    m.h15 = fmaf(wj1, yy, m.h15);
-    m.sw += w;
-    m.sxx += wxx;
-    m.sxy += wxy;
-    m.syy += wyy;
-    m.m40 = fmaf(wxx, xx, m.m40);
-    m.m31 = fmaf(wxx, xy, m.m31);
-    m.m22 = fmaf(wxx, yy, m.m22);
-    m.m13 = fmaf(wxy, yy, m.m13);
-    m.m04 = fmaf(wyy, yy, m.m04);
-    m.g0 = fmaf(we, j0, m.g0);
-    m.g1 = fmaf(we, j1, m.g1);
-    m.ge += we;
-    m.g3 = fmaf(we, xx, m.g3);
-    m.g4 = fmaf(we, xy, m.g4);
-    m.g5 = fmaf(we, yy, m.g5);
+__device__ __forceinline__ void visit2(Moments2& m, const Coef2& k, float za, float zb, float ca,
+                                       float cb, f32x2 DU, f32x2 RX, f32x2 RY, f32x2 RH, float thr) {
+    const f32x2 Z = pack(za, zb);
+    f32x2 X, Y, Hh;
+    local_xyz2(k, Z, DU, RX, RY, RH, X, Y, Hh);
+    const f32x2 XX = mul2(X, X), XY = mul2(X, Y), YY = mul2(Y, Y);
+    // eps = A/2 x^2 + B x y + C/2 y^2 - t_z - h
+    const f32x2 EPS = sub2(fma2(k.hA, XX, fma2(k.B, XY, fma2(k.hC, YY, k.ntz))), Hh);
+    const f32x2 E2 = mul2(EPS, EPS);
+    float da, db;
+    unpack(fma2(E2, k.invk, pack(ca, cb)), da, db);
+    float wa = rcp_approx(da), wb = rcp_approx(db);
+    if (REJECT) {
+        float ea, eb;
+        unpack(E2, ea, eb);
+        wa = ea <= thr ? wa : 0.f;
+        wb = eb <= thr ? wb : 0.f;
+    }
+    const f32x2 Wt = pack(wa, wb);
+    // -j0 = (B x + C y) h + y ; j1 = (A x + B y) h + x
+    const f32x2 NJ0 = fma2(fma2(k.B, X, mul2(k.C, Y)), Hh, Y);
+    const f32x2 J1 = fma2(fma2(k.A, X, mul2(k.B, Y)), Hh, X);
+    const f32x2 WE = mul2(Wt, EPS), WJ0 = mul2(Wt, NJ0), WJ1 = mul2(Wt, J1);
+    const f32x2 WXX = mul2(Wt, XX), WXY = mul2(Wt, XY), WYY = mul2(Wt, YY);
+    m.h00 = fma2(WJ0, NJ0, m.h00);
+    m.h01 = fma2(WJ0, J1, m.h01);
+    m.h11 = fma2(WJ1, J1, m.h11);
+    m.s0 = add2(m.s0, WJ0);
+    m.s1 = add2(m.s1, WJ1);
+    m.h03 = fma2(WJ0, XX, m.h03);
+    m.h04 = fma2(WJ0, XY, m.h04);
+    m.h05 = fma2(WJ0, YY, m.h05);
+    m.h13 = fma2(WJ1, XX, m.h13);
+    m.h14 = fma2(WJ1, XY, m.h14);
+    m.h15 = fma2(WJ1, YY, m.h15);
+    m.sw = add2(m.sw, Wt);
+    m.sxx = add2(m.sxx, WXX);
+    m.sxy = add2(m.sxy, WXY);
+    m.syy = add2(m.syy, WYY);
+    m.m40 = fma2(WXX, XX, m.m40);
+    m.m31 = fma2(WXX, XY, m.m31);
+    m.m22 = fma2(WXX, YY, m.m22);
+    m.m13 = fma2(WXY, YY, m.m13);
+    m.m04 = fma2(WYY, YY, m.m04);
+    m.g0 = fma2(WE, NJ0, m.g0);
+    m.g1 = fma2(WE, J1, m.g1);
+    m.ge = add2(m.ge, WE);
+    m.g3 = fma2(WE, XX, m.g3);
+    m.g4 = fma2(WE, XY, m.g4);
+    m.g5 = fma2(WE, YY, m.g5);
 }
 
-// Squared residual of a valid point, 0 for an invalid one (rejection pre-pass).
-__device__ __forceinline__ float sq_residual(const Coef& k, float Z, float c, float du, float rx,
-                                             float ry, float rh) {
-    float x, y, h;
-    local_xyz(k, Z, du, rx, ry, rh, x, y, h);
-    const float eps = fmaf(k.hA, x * x, fmaf(k.B, x * y, fmaf(k.hC, y * y, -(h + k.tz))));
-    return c == 1.f ? eps * eps : 0.f;
+// Squared residuals of a pair, 0 for invalid points (rejection pre-pass).
+__device__ __forceinline__ float sq_residual2(const Coef2& k, float za, float zb, float ca,
+                                              float cb, f32x2 DU, f32x2 RX, f32x2 RY, f32x2 RH) {
+    f32x2 X, Y, Hh;
+    local_xyz2(k, pack(za, zb), DU, RX, RY, RH, X, Y, Hh);
+    const f32x2 EPS = sub2(fma2(k.hA, mul2(X, X), fma2(k.B, mul2(X, Y), fma2(k.hC, mul2(Y, Y), k.ntz))), Hh);
+    float ea, eb;
+    unpack(mul2(EPS, EPS), ea, eb);
+    return (ca == 1.f ? ea : 0.f) + (cb == 1.f ? eb : 0.f);
 }
 
 // Solves (J^T W J) b = J^T W eps from the 26 sums, b returned as the update
 // delta = -b.  Jacobi-scaled LDL^T: S = D H D, D = diag(H)^-1/2; singular when
 // a diagonal entry is <= 0 or a pivot of S is <= pivot_tol.
-__device__ __forceinline__ bool solve_update(const Moments& m, float pivot_tol, float delta[6]) {
+__device__ __forceinline__ bool solve_update(const Moments2& m, float wc, float ec, float pivot_tol,
+                                             float delta[6]) {
+    // fold the pairs; the centre point adds w_c to sum w and w_c eps_c to sum w eps
+    const float h00 = hsum(m.h00), h01 = -hsum(m.h01), h11 = hsum(m.h11);
+    const float s0 = hsum(m.s0), s1 = hsum(m.s1);
+    const float h03 = -hsum(m.h03), h04 = -hsum(m.h04), h05 = -hsum(m.h05);
+    const float h13 = hsum(m.h13), h14 = hsum(m.h14), h15 = hsum(m.h15);
+    const float sw = hsum(m.sw) + wc;
+    const float sxx = hsum(m.sxx), sxy = hsum(m.sxy), syy = hsum(m.syy);
+    const float m40 = hsum(m.m40), m31 = hsum(m.m31), m22 = hsum(m.m22), m13 = hsum(m.m13),
+                m04 = hsum(m.m04);
+    const float g0 = -hsum(m.g0), g1 = hsum(m.g1), ge = fmaf(wc, ec, hsum(m.ge));
+    const float g3 = hsum(m.g3), g4 = hsum(m.g4), g5 = hsum(m.g5);
     float H[6][6];
-    H[0][0] = m.h00; H[0][1] = m.h01; H[0][2] = -m.s0;
-    H[0][3] = 0.5f * m.h03; H[0][4] = m.h04; H[0][5] = 0.5f * m.h05;
-    H[1][1] = m.h11; H[1][2] = -m.s1;
-    H[1][3] = 0.5f * m.h13; H[1][4] = m.h14; H[1][5] = 0.5f * m.h15;
-    H[2][2] = m.sw; H[2][3] = -0.5f * m.sxx; H[2][4] = -m.sxy; H[2][5] = -0.5f * m.syy;
-    H[3][3] = 0.25f * m.m40; H[3][4] = 0.5f * m.m31; H[3][5] = 0.25f * m.m22;
-    H[4][4] = m.m22; H[4][5] = 0.5f * m.m13;
-    H[5][5] = 0.25f * m.m04;
-    const float g[6] = {m.g0, m.g1, -m.ge, 0.5f * m.g3, m.g4, 0.5f * m.g5};
+    H[0][0] = h00; H[0][1] = h01; H[0][2] = s0;
+    H[0][3] = 0.5f * h03; H[0][4] = h04; H[0][5] = 0.5f * h05;
+    H[1][1] = h11; H[1][2] = -s1;
+    H[1][3] = 0.5f * h13; H[1][4] = h14; H[1][5] = 0.5f * h15;
+    H[2][2] = sw; H[2][3] = -0.5f * sxx; H[2][4] = -sxy; H[2][5] = -0.5f * syy;
+    H[3][3] = 0.25f * m40; H[3][4] = 0.5f * m31; H[3][5] = 0.25f * m22;
+    H[4][4] = m22; H[4][5] = 0.5f * m13;
+    H[5][5] = 0.25f * m04;
+    const float g[6] = {g0, g1, -ge, 0.5f * g3, g4, 0.5f * g5};
     float D[6];
 #pragma unroll
     for (int i = 0; i < 6; i++) {
@@ -231,19 +274,76 @@ __device__ __forceinline__ void rotate_left(float R[9], float t0, float t1) {
     for (int i = 0; i < 9; i++) R[i] = o[i];
 }
 
+// Visits every symmetric pair of the window of the thread's pixel once.
+// zc, cc point at the pixel's own entries of the Z and c planes (row stride SW).
+// Rows dv = -r0 .. -s pair with rows -dv; the centre row pairs du < 0 with -du.
+template <int RW, typename F>
+__device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, int SW, int r, int s,
+                                              F&& f) {
+    const int r0 = (r / s) * s;
+    const f32x2 STEP = pack((float)s, -(float)s);
+    for (int dv = -r0; dv < 0; dv += s) {
+        const float *za = zc + dv * SW, *zb = zc - dv * SW;
+        const float *ca = cc + dv * SW, *cb = cc - dv * SW;
+        const f32x2 DV = pack((float)dv, -(float)dv);
+        f32x2 DU = pack(-(float)r0, (float)r0);
+        if (RW > 0 && PC_COL_UNROLL == 0) {
+#pragma unroll
+            for (int du = -RW; du <= RW; du++) {
+                f(za[du], zb[-du], ca[du], cb[-du], DU, DV);
+                DU = add2(DU, STEP);
+            }
+        } else if (RW > 0) {
+            PC_UNROLL(PC_COL_UNROLL)
+            for (int du = -RW; du <= RW; du++) {
+                f(za[du], zb[-du], ca[du], cb[-du], DU, DV);
+                DU = add2(DU, STEP);
+            }
+        } else {
+            for (int du = -r0; du <= r0; du += s) {
+                f(za[du], zb[-du], ca[du], cb[-du], DU, DV);
+                DU = add2(DU, STEP);
+            }
+        }
+    }
+    const f32x2 DV0 = 0ull;
+    f32x2 DU = pack(-(float)r0, (float)r0);
+    if (RW > 0 && PC_COL_UNROLL == 0) {
+#pragma unroll
+        for (int du = -RW; du < 0; du++) {
+            f(zc[du], zc[-du], cc[du], cc[-du], DU, DV0);
+            DU = add2(DU, STEP);
+        }
+    } else if (RW > 0) {
+        PC_UNROLL(PC_COL_UNROLL)
+        for (int du = -RW; du < 0; du++) {
+            f(zc[du], zc[-du], cc[du], cc[-du], DU, DV0);
+            DU = add2(DU, STEP);
+        }
+    } else {
+        for (int du = -r0; du < 0; du += s) {
+            f(zc[du], zc[-du], cc[du], cc[-du], DU, DV0);
+            DU = add2(DU, STEP);
+        }
+    }
+}
+
 // RW > 0: window radius fixed at compile time, dense window, columns unrolled.
 // RW == 0: radius and stride from cfg.
 template <int RW, bool REJECT>
-__global__ void __launch_bounds__(BLOCK_THREADS)
+__global__ void __launch_bounds__(BLOCK_THREADS, PC_MIN_BLOCKS)
     k_fit(const float* __restrict__ depth, int H, int W, Camera cam, FitConfig cfg,
           float* __restrict__ k1o, float* __restrict__ k2o, float* __restrict__ nrmo) {
-    extern __shared__ float2 tile[];
+    extern __shared__ float smem[];
     const int r = RW > 0 ? RW : cfg.r;
     const int s = RW > 0 ? 1 : cfg.stride;
-    const int r0 = (r / s) * s;   // first sampled offset is -r0
+    const int r0 = (r / s) * s;   // largest sampled offset
     const int halo = r > cfg.rn ? r : cfg.rn;
     const int SW = TILE_W + 2 * halo;
     const int SH = TILE_H + 2 * halo;
+    float* tz = smem;                       // Z plane, SH x SW
+    float* tcv = smem + SW * SH;            // c plane
+    int* rcnt = (int*)(tcv + SW * SH);      // valid window points per (tile row, pixel column)
     const int ub = blockIdx.x * TILE_W, vb = blockIdx.y * TILE_H;
     const int tid = threadIdx.y * TILE_W + threadIdx.x;
 
@@ -259,17 +359,29 @@ __global__ void __launch_bounds__(BLOCK_THREADS)
                 c = 1.f;
             }
         }
-        tile[i] = make_float2(z, c);
+        tz[i] = z;
+        tcv[i] = c;
+    }
+    __syncthreads();
+    // valid points of each window row segment (columns -r0..r0 on the stride)
+    for (int i = tid; i < SH * TILE_W; i += BLOCK_THREADS) {
+        const int row = i / TILE_W, col = i - row * TILE_W;
+        const float* c = tcv + row * SW + col + halo;
+        int n = 0;
+        for (int du = -r0; du <= r0; du += s) n += c[du] == 1.f;
+        rcnt[i] = n;
     }
     __syncthreads();
 
     const int u0 = ub + threadIdx.x, v0 = vb + threadIdx.y;
     if (u0 >= W || v0 >= H) return;
     const size_t out = (size_t)v0 * W + u0;
-    const float2* ctr = tile + (threadIdx.y + halo) * SW + threadIdx.x + halo;
-    const float Zp = ctr->x;
+    const int cidx = (threadIdx.y + halo) * SW + threadIdx.x + halo;
+    const float* zc = tz + cidx;
+    const float* cc = tcv + cidx;
+    const float Zp = *zc;
     const float ap = (float)u0 - cam.cx, bp = (float)v0 - cam.cy;
-    bool ok = ctr->y == 1.f;
+    bool ok = *cc == 1.f;
 
     // ---- initial normal: z = a x + b y + c over the valid (2rn+1)^2 patch
     float nx = 0.f, ny = 0.f, nz = 1.f;
@@ -277,13 +389,14 @@ __global__ void __launch_bounds__(BLOCK_THREADS)
         float n = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f, sxz = 0.f,
               syz = 0.f;
         for (int dv = -cfg.rn; dv <= cfg.rn; dv++) {
-            const float2* row = ctr + dv * SW;
+            const float* zr = zc + dv * SW;
+            const float* cr = cc + dv * SW;
             for (int du = -cfg.rn; du <= cfg.rn; du++) {
-                const float2 e = row[du];
-                if (e.y == 1.f) {
-                    const float dZ = e.x - Zp;
-                    const float X = fmaf((float)du, e.x, ap * dZ) * cam.ifx;
-                    const float Y = fmaf((float)dv, e.x, bp * dZ) * cam.ify;
+                if (cr[du] == 1.f) {
+                    const float Zi = zr[du];
+                    const float dZ = Zi - Zp;
+                    const float X = fmaf((float)du, Zi, ap * dZ) * cam.ifx;
+                    const float Y = fmaf((float)dv, Zi, bp * dZ) * cam.ify;
                     n += 1.f;
                     sx += X; sy += Y; sz += dZ;
                     sxx = fmaf(X, X, sxx); sxy = fmaf(X, Y, sxy); syy = fmaf(Y, Y, syy);
@@ -307,23 +420,16 @@ __global__ void __launch_bounds__(BLOCK_THREADS)
         }
     }
 
-    // ---- window count
+    // ---- window count (row segments counted above)
+    int cnt = 0;
     if (ok) {
-        int cnt = 0;
-        for (int dv = -r0; dv <= r; dv += s) {
-            const float2* row = ctr + dv * SW;
-            if (RW > 0) {
-#pragma unroll
-                for (int du = -RW; du <= RW; du++) cnt += row[du].y == 1.f;
-            } else {
-                for (int du = -r0; du <= r; du += s) cnt += row[du].y == 1.f;
-            }
-        }
+        const int* rc = rcnt + (threadIdx.y + halo) * TILE_W + threadIdx.x;
+        for (int dv = -r0; dv <= r0; dv += s) cnt += rc[dv * TILE_W];
         ok = cnt >= cfg.min_window;
     }
 
     float R[9];
-    float A = 0.f, B = 0.f, C = 0.f, tz = 0.f;
+    float A = 0.f, B = 0.f, C = 0.f, tz0 = 0.f;
     {
         // minimal rotation with R n = e_z: I + [w]x + [w]x^2/(1+n_z), w = n x e_z
         const float f = 1.f / (1.f + nz);
@@ -333,62 +439,51 @@ __global__ void __launch_bounds__(BLOCK_THREADS)
     }
 
     for (int it = 0; ok && it < cfg.T; it++) {
-        Coef k;
-        k.cx0 = R[0] * cam.ifx; k.cy0 = R[1] * cam.ify;
-        k.bx = fmaf(k.cx0, ap, fmaf(k.cy0, bp, R[2]));
-        k.cx1 = R[3] * cam.ifx; k.cy1 = R[4] * cam.ify;
-        k.by = fmaf(k.cx1, ap, fmaf(k.cy1, bp, R[5]));
-        k.cx2 = R[6] * cam.ifx; k.cy2 = R[7] * cam.ify;
-        k.bh = fmaf(k.cx2, ap, fmaf(k.cy2, bp, R[8]));
-        k.A = A; k.B = B; k.C = C; k.tz = tz;
-        k.hA = 0.5f * A; k.hC = 0.5f * C;
-        k.invk = cfg.invk; k.Zp = Zp;
+        Coef2 k;
+        const float cx0 = R[0] * cam.ifx, cy0 = R[1] * cam.ify;
+        const float cx1 = R[3] * cam.ifx, cy1 = R[4] * cam.ify;
+        const float cx2 = R[6] * cam.ifx, cy2 = R[7] * cam.ify;
+        k.cx0 = splat(cx0); k.cx1 = splat(cx1); k.cx2 = splat(cx2);
+        k.bx = splat(fmaf(cx0, ap, fmaf(cy0, bp, R[2])));
+        k.by = splat(fmaf(cx1, ap, fmaf(cy1, bp, R[5])));
+        k.bh = splat(fmaf(cx2, ap, fmaf(cy2, bp, R[8])));
+        k.A = splat(A); k.B = splat(B); k.C = splat(C);
+        k.hA = splat(0.5f * A); k.hC = splat(0.5f * C);
+        k.ntz = splat(-tz0);
+        k.invk = splat(cfg.invk);
+        k.nzp = splat(-Zp);
+        const f32x2 CY0 = splat(cy0), CY1 = splat(cy1), CY2 = splat(cy2);
+        // the centre point: p' = 0, so eps_c = -t_z and j_c = (0, 0, -1, 0, 0, 0)
+        const float ec = -tz0;
+        const float wc = rcp_approx(fmaf(ec * ec, cfg.invk, 1.f));
 
         float thr = 0.f;
         if (REJECT) {
             // MSE of the window at this iteration; keep eps^2 <= ratio * MSE
             float se = 0.f;
-            int cnt = 0;
-            for (int dv = -r0; dv <= r; dv += s) {
-                const float2* row = ctr + dv * SW;
-                const float fdv = (float)dv;
-                const float rx = fdv * k.cy0, ry = fdv * k.cy1, rh = fdv * k.cy2;
-                for (int du = -r0; du <= r; du += s) {
-                    const float2 e = row[du];
-                    se += sq_residual(k, e.x, e.y, (float)du, rx, ry, rh);
-                    cnt += e.y == 1.f;
-                }
-            }
+            for_each_pair<RW>(zc, cc, SW, r, s, [&](float za, float zb, float ca, float cb, f32x2 DU,
+                                                    f32x2 DV) {
+                se += sq_residual2(k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1), mul2(DV, CY2));
+            });
+            se += ec * ec;
             thr = cfg.reject_ratio * (se / (float)cnt);
         }
+        const float wcr = (REJECT && !(ec * ec <= thr)) ? 0.f : wc;
 
-        Moments m;
+        Moments2 m;
         zero(m);
-        for (int dv = -r0; dv <= r; dv += s) {
-            const float2* row = ctr + dv * SW;
-            const float fdv = (float)dv;
-            const float rx = fdv * k.cy0, ry = fdv * k.cy1, rh = fdv * k.cy2;
-            if (RW > 0) {
-#pragma unroll
-                for (int du = -RW; du <= RW; du++) {
-                    const float2 e = row[du];
-                    visit<REJECT>(m, k, e.x, e.y, (float)du, rx, ry, rh, thr);
-                }
-            } else {
-                for (int du = -r0; du <= r; du += s) {
-                    const float2 e = row[du];
-                    visit<REJECT>(m, k, e.x, e.y, (float)du, rx, ry, rh, thr);
-                }
-            }
-        }
+        for_each_pair<RW>(zc, cc, SW, r, s, [&](float za, float zb, float ca, float cb, f32x2 DU,
+                                                f32x2 DV) {
+            visit2<REJECT>(m, k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1), mul2(DV, CY2), thr);
+        });
 
         float dl[6];
-        if (!solve_update(m, cfg.pivot_tol, dl)) {
+        if (!solve_update(m, wcr, ec, cfg.pivot_tol, dl)) {
             ok = false;
             break;
         }
         rotate_left(R, dl[0], dl[1]);
-        tz += dl[2];
+        tz0 += dl[2];
         A += dl[3];
         B += dl[4];
         C += dl[5];

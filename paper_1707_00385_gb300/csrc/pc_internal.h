@@ -32,9 +32,11 @@ constexpr int BLOCK_THREADS = TILE_W * TILE_H;
 
 inline int halo_of(const FitConfig& c) { return c.r > c.rn ? c.r : c.rn; }
 
+// Z and c planes of the tile + halo, and per-row valid counts.
 inline size_t fit_smem_bytes(const FitConfig& c) {
     const int h = halo_of(c);
-    return (size_t)(TILE_W + 2 * h) * (TILE_H + 2 * h) * 2 * sizeof(float);
+    return (size_t)(TILE_W + 2 * h) * (TILE_H + 2 * h) * 2 * sizeof(float) +
+           (size_t)(TILE_H + 2 * h) * TILE_W * sizeof(int);
 }
 
 // Enqueues the fused per-pixel kernel for one H x W image on `stream`.
