@@ -5,13 +5,18 @@ FP32 (the per-pixel quadric fit of Spek, Li, Drummond, arXiv 1707.00385).
 One step = the whole method (back-projection, initial normal, 5 iterations,
 eigen step, refined normal) over a batch of FRAMES distinct frame buffers
 (about 157 MB of ranges, more than the 129 MB L2, so no step reads another's
-inputs from L2), one pc_compute launch per frame.
+inputs from L2), enqueued as one pc_compute_batch call (a CUDA graph: frame
+table copy, queue reset, one persistent kernel over all tiles).
 
 Prints one JSON line.  `value` is Mpixel/s over the device-timed region with
-inputs resident in HBM; `e2e` is the same metric through pc_compute_host with
+inputs resident in HBM; `per_frame_launches` is the same with one pc_compute
+launch per frame; `uneven_batch` runs 64 frames of mixed resolutions
+(320x240, 512x424 time-of-flight, 640x480, 1280x720) in one batch call
+against 64 plain launches; `e2e` is the metric through pc_compute_host with
 pinned host buffers (host-to-device ranges and device-to-host k1, k2, normals
-inside the timed region); `roofline` reports the kernel against the FP32 ALU
-peak; `cpu_baseline` times the FP64 oracle on a bounded sample on the host.
+inside the timed region); `roofline` reports the persistent kernel against
+the FP32 ALU peak; `cpu_baseline` times the FP64 oracle on a bounded sample
+on the host.
 
 --impl reference times the oracle alone, on the host cores, on the same
 workload (each step a bounded sample).
@@ -66,6 +71,19 @@ def scenes(n):
     return [synth.kinect_scene(seed) for seed in range(n)]
 
 
+UNEVEN_SIZES = [(240, 320, "kinect"), (424, 512, "tof"), (480, 640, "kinect"), (720, 1280, "kinect")]
+
+
+def uneven_scenes(per_size=2):
+    """Seeded frames of the four resolutions (seeds 1000+), per_size of each."""
+    import synth
+    out = []
+    for j, (h, w, noise) in enumerate(UNEVEN_SIZES):
+        for i in range(per_size):
+            out.append(synth.kinect_scene(1000 + 10 * j + i, H=h, W=w, noise=noise))
+    return out
+
+
 def counted_flop(depth, r=RADIUS, T=ITERS, rn=3):
     """Counted FP32 work of one frame: for every pixel with a valid range and
     enough valid neighbours, T * (101 |W_p| + 250) + 12 |N_p|, where |W_p| and
@@ -97,16 +115,17 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, if it was taken on the current kernel sources."""
+def recorded_traffic(frames):
+    """DRAM bytes of one persistent launch over `frames` 640x480 frames, from
+    the committed ncu summary (bytes per frame), if it was taken on the current
+    kernel sources (DRAM traffic grows with the frames a launch processes)."""
     p = os.path.join(ROOT, "profiles", "k_fit_r7_640x480_traffic.txt")
     if not os.path.exists(p):
         return None
     kv = dict(l.strip().split("=", 1) for l in open(p) if "=" in l and not l.startswith("#"))
     if kv.get("kernel_sources_sha256_16") != kernel_sources_hash():
         return None
-    return float(kv["dram_bytes_per_launch"])
+    return float(kv["dram_bytes_per_frame"]) * frames
 
 
 class Clocks:
@@ -250,33 +269,77 @@ def main():
     nrm = [torch.empty((H, W, 3), device=dev) for _ in range(F)]
     curv = pc.Curvature(*intr, window_radius=RADIUS, iterations=ITERS)
     stream = torch.cuda.Stream(device=dev)
+    batch_args = [(depth[i], intr, k1[i], k2[i], nrm[i]) for i in range(F)]
 
-    def step():
+    def step_batch():
+        curv.batch(batch_args, stream=stream)
+
+    def step_frames():
         for i in range(F):
             curv(depth[i], k1[i], k2[i], nrm[i], stream=stream)
 
-    # ---- device-timed region: inputs resident in HBM
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
+    def device_time(step, steps, clocks=None):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctxm = Clocks(local) if clocks is not None else None
+        if ctxm:
+            ctxm.__enter__()
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    ms = max_over_ranks(e0.elapsed_time(e1))
+        if ctxm:
+            ctxm.__exit__(None, None, None)
+            clocks.update(ctxm.summary())
+        barrier()
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1))
+
+    # ---- device-timed region: inputs resident in HBM, one batch call per step
+    clocks = {}
+    ms = device_time(step_batch, args.steps, clocks)
     ms_step = ms / args.steps
     px_total = float(world) * args.steps * F * H * W
     value = px_total / (ms / 1e3) / 1e6
-    launch_ms = ms_step / F   # one kernel per frame, launched back to back
-    clocks = clk.summary()
+    launch_ms = ms_step   # one persistent kernel per step
+    # the same frames, one pc_compute launch per frame
+    ms_pf = device_time(step_frames, max(2, args.steps // 2))
+    pf_value = float(world) * max(2, args.steps // 2) * F * H * W / (ms_pf / 1e3) / 1e6
+
+    # ---- uneven frames (four resolutions): one batch call vs plain launches
+    un = uneven_scenes(2)
+    un_dev = []
+    for i in range(64):
+        s_ = un[i % len(un)]
+        d_ = torch.from_numpy(s_.depth).to(dev)
+        un_dev.append((d_, s_.intrinsics, torch.empty_like(d_), torch.empty_like(d_),
+                       torch.empty(d_.shape + (3,), device=dev)))
+    un_px = sum(a[0].numel() for a in un_dev)
+    un_ctx = [pc.Curvature(*s_.intrinsics, window_radius=RADIUS, iterations=ITERS) for s_ in un]
+
+    def step_un_batch():
+        curv.batch(un_dev, stream=stream)
+
+    def step_un_frames():
+        for i, (d_, _, a_, b_, n_) in enumerate(un_dev):
+            un_ctx[i % len(un)](d_, a_, b_, n_, stream=stream)
+
+    ub_steps = max(2, args.steps // 4)
+    ms_ub = device_time(step_un_batch, ub_steps)
+    ms_uf = device_time(step_un_frames, ub_steps)
+    uneven = {"frames": 64, "resolutions": [f"{w}x{h}" for h, w, _ in UNEVEN_SIZES],
+              "distinct_scenes": len(un), "pixels": un_px,
+              "batch_frames_per_s": float(world) * 64 * ub_steps / (ms_ub / 1e3),
+              "plain_launch_frames_per_s": float(world) * 64 * ub_steps / (ms_uf / 1e3),
+              "batch_ms": ms_ub / ub_steps, "plain_ms": ms_uf / ub_steps}
+    for c_ in un_ctx:
+        c_.close()
 
     # ---- end to end through the host-memory entry point (pinned buffers)
     hd = [torch.from_numpy(h).pin_memory() for h in host]
@@ -301,21 +364,22 @@ def main():
     barrier()
     e2e_s = max_over_ranks(t1 - t0)
     e2e_val = float(world) * e2e_steps * F * H * W / e2e_s / 1e6
-    # results of both paths agree (same kernel, same inputs)
-    same = bool(torch.equal(hk1[0], k1[0].cpu()) or np.array_equal(hk1[0].numpy(), k1[0].cpu().numpy(),
-                                                                  equal_nan=True))
+    # host path and batched device path give the same numbers
+    step_batch()
+    torch.cuda.synchronize()
+    same = bool(np.array_equal(hk1[0].numpy(), k1[0].cpu().numpy(), equal_nan=True))
 
-    # ---- roofline of the fused kernel: counted FP32 work vs the FP32 ALU peak
+    # ---- roofline of the persistent kernel: counted FP32 work vs the FP32 ALU peak
     props = torch.cuda.get_device_properties(dev)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = (flop_step / F) / (launch_ms / 1e3) / 1e12
+    achieved = flop_step / (launch_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": recorded_traffic(),
-            "kernel": "k_fit<7> (fused normal + IRLS + eigen), one launch per 640x480 frame",
+            "traffic": recorded_traffic(F),
+            "kernel": f"k_fit_batch<7> (fused normal + IRLS + eigen), one persistent launch over {F} 640x480 frames",
             "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                           f"{sm_max:.0f} MHz max SM clock (derived)",
-            "launch_ms": launch_ms, "counted_flop_per_launch": flop_step / F}
+            "launch_ms": launch_ms, "counted_flop_per_launch": flop_step}
 
     line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -330,7 +394,9 @@ def main():
             "e2e": {"value": e2e_val, "unit": "Mpixel/s", "h2d_bytes_per_step": F * H * W * 4,
                     "d2h_bytes_per_step": F * H * W * 4 * 5, "api": "pc_compute_host",
                     "matches_device_path": same},
-            "gpu_launches": args.steps * F,
+            "per_frame_launches": {"value": pf_value, "unit": "Mpixel/s", "ms_per_frame": ms_pf / max(2, args.steps // 2) / F},
+            "uneven_batch": uneven,
+            "gpu_launches": args.steps,
             "clocks": clocks,
             "roofline": roof}
     if rank == 0 and not args.no_cpu_baseline:

@@ -65,6 +65,7 @@ typedef enum pc_status {
 #define PC_MAX_NORMAL_RADIUS 8   /* initial-normal patch radius */
 #define PC_MAX_ITERATIONS 64     /* re-weighted iterations */
 #define PC_MAX_DIM 16384         /* H and W */
+#define PC_MAX_BATCH 4096        /* frames per pc_compute_batch call */
 
 /* Tunable parameters of the method.  Fill with pc_params_default() first. */
 typedef struct pc_params {
@@ -81,6 +82,9 @@ typedef struct pc_params {
                             above 1/pivot_tol).  Default 1e-5: single-precision moment sums
                             carry ~1e-6 relative error, so smaller pivots are not resolved */
     int min_window;      /* fewest valid window points accepted. Default 6 */
+    int batch_graph;     /* 1 = pc_compute_batch replays a CUDA graph (copy of the frame table,
+                            reset of the tile queue, persistent kernel) captured once per
+                            table capacity; 0 = enqueue the three steps directly. Default 1 */
 } pc_params;
 
 /* Writes the defaults above into *p (no-op for NULL). */
@@ -111,8 +115,32 @@ pc_status pc_compute(pc_ctx* ctx, const float* depth, int H, int W, void* stream
 pc_status pc_compute_host(pc_ctx* ctx, const float* depth_host, int H, int W, void* stream,
                           float* k1_host, float* k2_host, float* normal_host);
 
-/* Frees the context and its staging buffers (synchronising the device first
- * when it owns any).  NULL is a no-op returning PC_OK. */
+/* One frame of a batch: its own size, intrinsics (pixels) and device buffers,
+ * with the layouts of pc_compute. */
+typedef struct pc_frame {
+    const float* depth;  /* device, H*W floats */
+    int H, W;            /* 0 <= H, W <= PC_MAX_DIM; an empty frame is skipped */
+    float fx, fy, cx, cy;
+    float* k1;           /* device, H*W floats */
+    float* k2;           /* device, H*W floats */
+    float* normal;       /* device, H*W*3 floats, or NULL */
+} pc_frame;
+
+/* The method on n frames of any sizes and intrinsics (0 <= n <= PC_MAX_BATCH)
+ * in one persistent launch over a flattened queue of (frame, tile) items,
+ * with the window radius, iterations and parameters of ctx.  `frames` is host
+ * memory, read during the call.  The frame table is staged through one of two
+ * page-locked buffers owned by ctx and copied into device scratch owned by ctx
+ * (allocated on the first call, grown to the next power of two of n; the call
+ * may wait for the batch before the previous one to finish reading its
+ * buffer).  Results equal those of pc_compute frame by frame, bit for bit.
+ * Successive batch calls on one ctx must use one stream, or synchronise in
+ * between, because the device scratch is shared. */
+pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream);
+
+/* Frees the context, its staging buffers, batch scratch and graphs
+ * (synchronising the device first when it owns any).  NULL is a no-op
+ * returning PC_OK. */
 pc_status pc_destroy(pc_ctx* ctx);
 
 /* Static description of a status code. */

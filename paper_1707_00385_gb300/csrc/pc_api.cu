@@ -1,6 +1,6 @@
 // pc_api.cu -- host runtime behind the C ABI declared in include/pcurv.h:
-// argument checks, the context, staging buffers for host-memory calls, and
-// the choice of kernel instantiation.
+// argument checks, the context, staging buffers for host-memory calls, the
+// batch scratch and its CUDA graphs, and the choice of kernel instantiation.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -9,6 +9,29 @@
 
 #include "../../include/pcurv.h"
 #include "pc_internal.h"
+
+namespace {
+
+// Device scratch of pc_compute_batch: the frame table and the tile counter,
+// two page-locked staging copies of the table (alternating between calls so
+// that a call rarely waits), and one graph per staging copy.
+struct BatchScratch {
+    int device = -1;
+    int cap = 0;                              // frames the table holds
+    pcurv::BatchTable* d_table = nullptr;     // device
+    unsigned* d_counter = nullptr;            // device
+    pcurv::BatchTable* h_table[2] = {nullptr, nullptr};  // page-locked host
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    bool pending[2] = {false, false};
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_grid[2] = {0, 0};
+    int graph_cap[2] = {0, 0};
+    cudaStream_t capture = nullptr;           // private stream used only for capture
+    int grid = 0;                             // persistent CTAs
+    int next = 0;                             // staging copy of the next call
+};
+
+}  // namespace
 
 struct pc_ctx {
     pcurv::Camera cam;
@@ -21,6 +44,7 @@ struct pc_ctx {
     float* d_k1 = nullptr;
     float* d_k2 = nullptr;
     float* d_normal = nullptr;
+    BatchScratch batch;
     char last_error[256] = {0};
 };
 
@@ -39,7 +63,7 @@ bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+        cudaGetLastError();  // clear the error of an unknown pointer
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
@@ -54,6 +78,7 @@ pc_status check_params(const pc_params& p) {
     if (!(finite_f(p.det_tol) && p.det_tol >= 0.f)) return PC_ERR_INVALID_ARG;
     if (!(finite_f(p.pivot_tol) && p.pivot_tol >= 0.f)) return PC_ERR_INVALID_ARG;
     if (p.min_window < 6) return PC_ERR_INVALID_ARG;  // six parameters need six points
+    if (p.batch_graph != 0 && p.batch_graph != 1) return PC_ERR_INVALID_ARG;
     return PC_OK;
 }
 
@@ -62,19 +87,61 @@ pc_status check_image(int H, int W) {
     return PC_OK;
 }
 
+bool valid_intrinsics(float fx, float fy, float cx, float cy) {
+    return finite_f(fx) && finite_f(fy) && finite_f(cx) && finite_f(cy) && fx > 0.f && fy > 0.f;
+}
+
+// Device buffers of one frame: present, aligned, on the device.
+pc_status check_buffers(const float* depth, const float* k1, const float* k2, const float* normal) {
+    if (!depth || !k1 || !k2) return PC_ERR_INVALID_ARG;
+    if (!aligned4(depth) || !aligned4(k1) || !aligned4(k2) || !aligned4(normal)) return PC_ERR_INVALID_ARG;
+    if (!is_device_ptr(depth) || !is_device_ptr(k1) || !is_device_ptr(k2) ||
+        (normal && !is_device_ptr(normal)))
+        return PC_ERR_INVALID_ARG;
+    return PC_OK;
+}
+
+void release_batch(BatchScratch& b) {
+    for (int i = 0; i < 2; i++) {
+        if (b.pending[i]) cudaEventSynchronize(b.done[i]);
+        b.pending[i] = false;
+        if (b.graph[i]) cudaGraphExecDestroy(b.graph[i]);
+        b.graph[i] = nullptr;
+        b.graph_grid[i] = b.graph_cap[i] = 0;
+        if (b.h_table[i]) cudaFreeHost(b.h_table[i]);
+        b.h_table[i] = nullptr;
+        if (b.done[i]) cudaEventDestroy(b.done[i]);
+        b.done[i] = nullptr;
+    }
+    cudaFree(b.d_table);
+    cudaFree(b.d_counter);
+    b.d_table = nullptr;
+    b.d_counter = nullptr;
+    if (b.capture) cudaStreamDestroy(b.capture);
+    b.capture = nullptr;
+    b.cap = 0;
+    b.grid = 0;
+    b.device = -1;
+}
+
+int round_up_pow2(int n) {
+    int c = 1;
+    while (c < n) c <<= 1;
+    return c;
+}
+
 }  // namespace
 
 namespace pcurv {
 
-cudaError_t launch_fit(const float* depth, int H, int W, const Camera& cam, const FitConfig& cfg,
-                       float* k1, float* k2, float* normal, cudaStream_t stream) {
-    if (cfg.stride == 1 && cfg.r >= 1 && cfg.r <= 4)
-        return launch_fit_r1_4(depth, H, W, cam, cfg, k1, k2, normal, stream);
-    if (cfg.stride == 1 && cfg.r >= 5 && cfg.r <= 8)
-        return launch_fit_r5_8(depth, H, W, cam, cfg, k1, k2, normal, stream);
-    if (cfg.stride == 1 && cfg.r >= 9 && cfg.r <= 12)
-        return launch_fit_r9_12(depth, H, W, cam, cfg, k1, k2, normal, stream);
-    return launch_fit_generic(depth, H, W, cam, cfg, k1, k2, normal, stream);
+const KernelOps* select_ops(const FitConfig& cfg) {
+    const KernelOps* k = nullptr;
+    if (cfg.stride == 1) {
+        if (cfg.r >= 1 && cfg.r <= 4) k = ops_r1_4(cfg.r);
+        else if (cfg.r >= 5 && cfg.r <= 8) k = ops_r5_8(cfg.r);
+        else if (cfg.r >= 9 && cfg.r <= 12) k = ops_r9_12(cfg.r);
+    }
+    return k ? k : ops_generic();
 }
 
 }  // namespace pcurv
@@ -91,14 +158,14 @@ void pc_params_default(pc_params* p) {
     p->det_tol = 1e-6f;
     p->pivot_tol = 1e-5f;
     p->min_window = 6;
+    p->batch_graph = 1;
 }
 
 pc_status pc_create(float fx, float fy, float cx, float cy, int window_radius, int iterations,
                     const pc_params* params, pc_ctx** out) {
     if (!out) return PC_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!(finite_f(fx) && finite_f(fy) && finite_f(cx) && finite_f(cy) && fx > 0.f && fy > 0.f))
-        return PC_ERR_INVALID_ARG;
+    if (!valid_intrinsics(fx, fy, cx, cy)) return PC_ERR_INVALID_ARG;
     if (window_radius < 1 || window_radius > PC_MAX_RADIUS) return PC_ERR_INVALID_ARG;
     if (iterations < 0 || iterations > PC_MAX_ITERATIONS) return PC_ERR_INVALID_ARG;
     pc_params p;
@@ -122,14 +189,9 @@ pc_status pc_compute(pc_ctx* ctx, const float* depth, int H, int W, void* stream
     pc_status st = check_image(H, W);
     if (st != PC_OK) return st;
     if (H == 0 || W == 0) return PC_OK;
-    if (!depth || !k1_out || !k2_out) return PC_ERR_INVALID_ARG;
-    if (!aligned4(depth) || !aligned4(k1_out) || !aligned4(k2_out) || !aligned4(normal_out))
-        return PC_ERR_INVALID_ARG;
-    if (!is_device_ptr(depth) || !is_device_ptr(k1_out) || !is_device_ptr(k2_out) ||
-        (normal_out && !is_device_ptr(normal_out)))
-        return PC_ERR_INVALID_ARG;
-    const cudaError_t e = pcurv::launch_fit(depth, H, W, ctx->cam, ctx->cfg, k1_out, k2_out,
-                                            normal_out, (cudaStream_t)stream);
+    if ((st = check_buffers(depth, k1_out, k2_out, normal_out)) != PC_OK) return st;
+    const pcurv::FrameArgs f{depth, H, W, ctx->cam, k1_out, k2_out, normal_out};
+    const cudaError_t e = pcurv::select_ops(ctx->cfg)->fit(f, ctx->cfg, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute launch");
     return PC_OK;
 }
@@ -175,8 +237,9 @@ pc_status pc_compute_host(pc_ctx* ctx, const float* depth_host, int H, int W, vo
     if ((e = cudaMemcpyAsync(ctx->d_depth, depth_host, npx * sizeof(float), cudaMemcpyHostToDevice,
                              s)) != cudaSuccess)
         return cuda_fail(ctx, e, "depth H2D");
-    e = pcurv::launch_fit(ctx->d_depth, H, W, ctx->cam, ctx->cfg, ctx->d_k1, ctx->d_k2,
-                          normal_host ? ctx->d_normal : nullptr, s);
+    const pcurv::FrameArgs f{ctx->d_depth, H, W, ctx->cam, ctx->d_k1, ctx->d_k2,
+                             normal_host ? ctx->d_normal : nullptr};
+    e = pcurv::select_ops(ctx->cfg)->fit(f, ctx->cfg, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_host launch");
     if ((e = cudaMemcpyAsync(k1_host, ctx->d_k1, npx * sizeof(float), cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess ||
@@ -190,12 +253,134 @@ pc_status pc_compute_host(pc_ctx* ctx, const float* depth_host, int H, int W, vo
     return PC_OK;
 }
 
+// Batch scratch for at least n frames on the current device.
+static pc_status ensure_batch(pc_ctx* ctx, int n) {
+    BatchScratch& b = ctx->batch;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetDevice");
+    if (b.device == dev && b.cap >= n) return PC_OK;
+    release_batch(b);
+    const int cap = round_up_pow2(n < 16 ? 16 : n);
+    const size_t bytes = pcurv::batch_table_bytes(cap);
+    const pcurv::KernelOps* ops = pcurv::select_ops(ctx->cfg);
+    int sms = 0, bps = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = ops->occupancy(ctx->cfg, &bps)) != cudaSuccess)
+        return cuda_fail(ctx, e, "batch occupancy");
+    if ((e = cudaMalloc(&b.d_table, bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&b.d_counter, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaHostAlloc(&b.h_table[0], bytes, cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaHostAlloc(&b.h_table[1], bytes, cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b.done[0], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b.done[1], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&b.capture, cudaStreamNonBlocking)) != cudaSuccess) {
+        release_batch(b);
+        return cuda_fail(ctx, e, "batch scratch");
+    }
+    b.device = dev;
+    b.cap = cap;
+    b.grid = sms * (bps > 0 ? bps : 1);
+    return PC_OK;
+}
+
+// Copy of the staged table, queue reset and persistent kernel, on `s`.
+static cudaError_t enqueue_batch(pc_ctx* ctx, int slot, size_t bytes, cudaStream_t s) {
+    BatchScratch& b = ctx->batch;
+    cudaError_t e = cudaMemcpyAsync(b.d_table, b.h_table[slot], bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    return pcurv::select_ops(ctx->cfg)->batch(b.d_table, b.d_counter, b.grid, ctx->cfg, s);
+}
+
+// The graph of staging copy `slot` (captured on the private stream once per capacity).
+static pc_status ensure_graph(pc_ctx* ctx, int slot) {
+    BatchScratch& b = ctx->batch;
+    if (b.graph[slot] && b.graph_cap[slot] == b.cap && b.graph_grid[slot] == b.grid) return PC_OK;
+    if (b.graph[slot]) cudaGraphExecDestroy(b.graph[slot]);
+    b.graph[slot] = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b.capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture begin");
+    const cudaError_t e1 = enqueue_batch(ctx, slot, pcurv::batch_table_bytes(b.cap), b.capture);
+    e = cudaStreamEndCapture(b.capture, &g);
+    if (e1 != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(ctx, e1 != cudaSuccess ? e1 : e, "graph capture");
+    }
+    e = cudaGraphInstantiate(&b.graph[slot], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b.graph[slot] = nullptr;
+        return cuda_fail(ctx, e, "graph instantiate");
+    }
+    b.graph_cap[slot] = b.cap;
+    b.graph_grid[slot] = b.grid;
+    return PC_OK;
+}
+
+pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream) {
+    if (!ctx || n < 0 || n > PC_MAX_BATCH || (n > 0 && !frames)) return PC_ERR_INVALID_ARG;
+    long long total = 0;
+    int live = 0;
+    for (int i = 0; i < n; i++) {
+        const pc_frame& fr = frames[i];
+        pc_status st = check_image(fr.H, fr.W);
+        if (st != PC_OK) return st;
+        if (fr.H == 0 || fr.W == 0) continue;
+        if (!valid_intrinsics(fr.fx, fr.fy, fr.cx, fr.cy)) return PC_ERR_INVALID_ARG;
+        if ((st = check_buffers(fr.depth, fr.k1, fr.k2, fr.normal)) != PC_OK) return st;
+        total += (long long)((fr.W + pcurv::TILE_W - 1) / pcurv::TILE_W) *
+                 ((fr.H + pcurv::TILE_H - 1) / pcurv::TILE_H);
+        live++;
+    }
+    if (live == 0) return PC_OK;
+    if (total > 0x7fffffffLL) return PC_ERR_INVALID_ARG;
+    pc_status st = ensure_batch(ctx, live);
+    if (st != PC_OK) return st;
+    BatchScratch& b = ctx->batch;
+    const int slot = b.next;
+    b.next ^= 1;
+    cudaError_t e;
+    if (b.pending[slot]) {
+        // the batch before last may still be reading this staging copy
+        if ((e = cudaEventSynchronize(b.done[slot])) != cudaSuccess) return cuda_fail(ctx, e, "batch wait");
+        b.pending[slot] = false;
+    }
+    pcurv::BatchTable* t = b.h_table[slot];
+    int k = 0, begin = 0;
+    for (int i = 0; i < n; i++) {
+        const pc_frame& fr = frames[i];
+        if (fr.H == 0 || fr.W == 0) continue;
+        pcurv::BatchFrame& d = t->frames[k++];
+        d.f = pcurv::FrameArgs{fr.depth, fr.H, fr.W,
+                               pcurv::Camera{fr.fx, fr.fy, fr.cx, fr.cy, 1.f / fr.fx, 1.f / fr.fy},
+                               fr.k1, fr.k2, fr.normal};
+        d.tiles_x = (fr.W + pcurv::TILE_W - 1) / pcurv::TILE_W;
+        d.tile_begin = begin;
+        begin += d.tiles_x * ((fr.H + pcurv::TILE_H - 1) / pcurv::TILE_H);
+    }
+    t->nframes = live;
+    t->total_tiles = begin;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->params.batch_graph) {
+        if ((st = ensure_graph(ctx, slot)) != PC_OK) return st;
+        if ((e = cudaGraphLaunch(b.graph[slot], s)) != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+    } else if ((e = enqueue_batch(ctx, slot, pcurv::batch_table_bytes(live), s)) != cudaSuccess) {
+        return cuda_fail(ctx, e, "batch launch");
+    }
+    if ((e = cudaEventRecord(b.done[slot], s)) != cudaSuccess) return cuda_fail(ctx, e, "batch event");
+    b.pending[slot] = true;
+    return PC_OK;
+}
+
 pc_status pc_destroy(pc_ctx* ctx) {
     if (!ctx) return PC_OK;
     if (ctx->stage_px) {
         cudaDeviceSynchronize();
         free_stage(ctx);
     }
+    if (ctx->batch.device >= 0) release_batch(ctx->batch);
     delete ctx;
     return PC_OK;
 }

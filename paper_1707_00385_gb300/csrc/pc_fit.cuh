@@ -287,14 +287,12 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
         const float *ca = cc + dv * SW, *cb = cc - dv * SW;
         const f32x2 DV = pack((float)dv, -(float)dv);
         f32x2 DU = pack(-(float)r0, (float)r0);
-        if (RW > 0 && PC_COL_UNROLL == 0) {
-#pragma unroll
-            for (int du = -RW; du <= RW; du++) {
-                f(za[du], zb[-du], ca[du], cb[-du], DU, DV);
-                DU = add2(DU, STEP);
-            }
-        } else if (RW > 0) {
+        if (RW > 0) {
+#if PC_COL_UNROLL > 0
             PC_UNROLL(PC_COL_UNROLL)
+#else
+#pragma unroll
+#endif
             for (int du = -RW; du <= RW; du++) {
                 f(za[du], zb[-du], ca[du], cb[-du], DU, DV);
                 DU = add2(DU, STEP);
@@ -308,14 +306,12 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
     }
     const f32x2 DV0 = 0ull;
     f32x2 DU = pack(-(float)r0, (float)r0);
-    if (RW > 0 && PC_COL_UNROLL == 0) {
-#pragma unroll
-        for (int du = -RW; du < 0; du++) {
-            f(zc[du], zc[-du], cc[du], cc[-du], DU, DV0);
-            DU = add2(DU, STEP);
-        }
-    } else if (RW > 0) {
+    if (RW > 0) {
+#if PC_COL_UNROLL > 0
         PC_UNROLL(PC_COL_UNROLL)
+#else
+#pragma unroll
+#endif
         for (int du = -RW; du < 0; du++) {
             f(zc[du], zc[-du], cc[du], cc[-du], DU, DV0);
             DU = add2(DU, STEP);
@@ -328,13 +324,21 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
     }
 }
 
+// The whole method for one 32 x 8 output tile (tile column tx_, tile row ty_)
+// of frame f.  Called by every thread of the CTA; contains two __syncthreads
+// and leaves shared memory in use until it returns (callers that reuse smem
+// synchronise first).
 // RW > 0: window radius fixed at compile time, dense window, columns unrolled.
 // RW == 0: radius and stride from cfg.
 template <int RW, bool REJECT>
-__global__ void __launch_bounds__(BLOCK_THREADS, PC_MIN_BLOCKS)
-    k_fit(const float* __restrict__ depth, int H, int W, Camera cam, FitConfig cfg,
-          float* __restrict__ k1o, float* __restrict__ k2o, float* __restrict__ nrmo) {
-    extern __shared__ float smem[];
+__device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cfg, int tx_, int ty_,
+                                         float* smem) {
+    const float* __restrict__ depth = f.depth;
+    const int H = f.H, W = f.W;
+    const Camera cam = f.cam;
+    float* __restrict__ k1o = f.k1;
+    float* __restrict__ k2o = f.k2;
+    float* __restrict__ nrmo = f.normal;
     const int r = RW > 0 ? RW : cfg.r;
     const int s = RW > 0 ? 1 : cfg.stride;
     const int r0 = (r / s) * s;   // largest sampled offset
@@ -344,7 +348,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS, PC_MIN_BLOCKS)
     float* tz = smem;                       // Z plane, SH x SW
     float* tcv = smem + SW * SH;            // c plane
     int* rcnt = (int*)(tcv + SW * SH);      // valid window points per (tile row, pixel column)
-    const int ub = blockIdx.x * TILE_W, vb = blockIdx.y * TILE_H;
+    const int ub = tx_ * TILE_W, vb = ty_ * TILE_H;
     const int tid = threadIdx.y * TILE_W + threadIdx.x;
 
     // stage the tile + halo (Sec. 3.2, first item: the range image)
@@ -374,7 +378,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS, PC_MIN_BLOCKS)
     __syncthreads();
 
     const int u0 = ub + threadIdx.x, v0 = vb + threadIdx.y;
-    if (u0 >= W || v0 >= H) return;
+    if (u0 >= W || v0 >= H) return;   // no barrier follows in this function
     const size_t out = (size_t)v0 * W + u0;
     const int cidx = (threadIdx.y + halo) * SW + threadIdx.x + halo;
     const float* zc = tz + cidx;
@@ -512,17 +516,72 @@ __global__ void __launch_bounds__(BLOCK_THREADS, PC_MIN_BLOCKS)
     }
 }
 
+template <int RW, bool REJECT>
+__global__ void __launch_bounds__(BLOCK_THREADS, PC_MIN_BLOCKS) k_fit(FrameArgs f, FitConfig cfg) {
+    extern __shared__ float smem[];
+    fit_tile<RW, REJECT>(f, cfg, blockIdx.x, blockIdx.y, smem);
+}
+
+// Persistent form over many frames: the CTAs take (frame, tile) items from a
+// flattened queue with one atomic per tile until it is empty.  The header and
+// descriptors live in device memory (BatchTable); *next_tile must be 0 at launch.
+template <int RW, bool REJECT>
+__global__ void __launch_bounds__(BLOCK_THREADS, PC_MIN_BLOCKS)
+    k_fit_batch(const BatchTable* __restrict__ table, unsigned* __restrict__ next_tile, FitConfig cfg) {
+    extern __shared__ float smem[];
+    __shared__ int s_tile;
+    const int nframes = table->nframes, total = table->total_tiles;
+    const BatchFrame* __restrict__ fr = table->frames;
+    for (;;) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) s_tile = (int)atomicAdd(next_tile, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= total) break;  // uniform over the CTA
+        // last frame whose first tile is <= t
+        int lo = 0, hi = nframes - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (fr[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+        }
+        const int local = t - fr[lo].tile_begin, tiles_x = fr[lo].tiles_x;
+        const int ty_ = local / tiles_x;
+        fit_tile<RW, REJECT>(fr[lo].f, cfg, local - ty_ * tiles_x, ty_, smem);
+        __syncthreads();  // shared memory and s_tile are reused by the next tile
+    }
+}
+
 template <int RW>
-cudaError_t launch_fit_rw(const float* depth, int H, int W, const Camera& cam, const FitConfig& cfg,
-                          float* k1, float* k2, float* normal, cudaStream_t stream) {
+cudaError_t launch_fit_rw(const FrameArgs& f, const FitConfig& cfg, cudaStream_t stream) {
     const dim3 block(TILE_W, TILE_H);
-    const dim3 grid((W + TILE_W - 1) / TILE_W, (H + TILE_H - 1) / TILE_H);
+    const dim3 grid((f.W + TILE_W - 1) / TILE_W, (f.H + TILE_H - 1) / TILE_H);
     const size_t smem = fit_smem_bytes(cfg);
     if (cfg.reject)
-        k_fit<RW, true><<<grid, block, smem, stream>>>(depth, H, W, cam, cfg, k1, k2, normal);
+        k_fit<RW, true><<<grid, block, smem, stream>>>(f, cfg);
     else
-        k_fit<RW, false><<<grid, block, smem, stream>>>(depth, H, W, cam, cfg, k1, k2, normal);
+        k_fit<RW, false><<<grid, block, smem, stream>>>(f, cfg);
     return cudaGetLastError();
+}
+
+template <int RW>
+cudaError_t launch_batch_rw(const BatchTable* table, unsigned* next_tile, int grid, const FitConfig& cfg,
+                            cudaStream_t stream) {
+    const dim3 block(TILE_W, TILE_H);
+    const size_t smem = fit_smem_bytes(cfg);
+    if (cfg.reject)
+        k_fit_batch<RW, true><<<grid, block, smem, stream>>>(table, next_tile, cfg);
+    else
+        k_fit_batch<RW, false><<<grid, block, smem, stream>>>(table, next_tile, cfg);
+    return cudaGetLastError();
+}
+
+template <int RW>
+cudaError_t occupancy_rw(const FitConfig& cfg, int* blocks_per_sm) {
+    const size_t smem = fit_smem_bytes(cfg);
+    return cfg.reject
+               ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fit_batch<RW, true>,
+                                                               BLOCK_THREADS, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fit_batch<RW, false>,
+                                                               BLOCK_THREADS, smem);
 }
 
 }  // namespace pcurv

@@ -1,13 +1,12 @@
-// The fused kernel with the window radius and sampling stride read at run
+// The fused kernels with the window radius and sampling stride read at run
 // time (radii above the unrolled set, and sparse windows).
 #include "pc_fit.cuh"
 
 namespace pcurv {
 
-cudaError_t launch_fit_generic(const float* depth, int H, int W, const Camera& cam,
-                               const FitConfig& cfg, float* k1, float* k2, float* normal,
-                               cudaStream_t stream) {
-    return launch_fit_rw<0>(depth, H, W, cam, cfg, k1, k2, normal, stream);
+const KernelOps* ops_generic() {
+    static const KernelOps k = {launch_fit_rw<0>, launch_batch_rw<0>, occupancy_rw<0>};
+    return &k;
 }
 
 }  // namespace pcurv

@@ -1,17 +1,19 @@
-// Instantiations of the fused kernel for window radii 1..4 (dense window).
+// Instantiations of the fused kernels for window radii 1..4 (dense window).
 #include "pc_fit.cuh"
 
 namespace pcurv {
 
-cudaError_t launch_fit_r1_4(const float* depth, int H, int W, const Camera& cam,
-                            const FitConfig& cfg, float* k1, float* k2, float* normal,
-                            cudaStream_t stream) {
-    switch (cfg.r) {
-        case 1: return launch_fit_rw<1>(depth, H, W, cam, cfg, k1, k2, normal, stream);
-        case 2: return launch_fit_rw<2>(depth, H, W, cam, cfg, k1, k2, normal, stream);
-        case 3: return launch_fit_rw<3>(depth, H, W, cam, cfg, k1, k2, normal, stream);
-        case 4: return launch_fit_rw<4>(depth, H, W, cam, cfg, k1, k2, normal, stream);
-        default: return cudaErrorInvalidValue;
+const KernelOps* ops_r1_4(int r) {
+    static const KernelOps k1 = {launch_fit_rw<1>, launch_batch_rw<1>, occupancy_rw<1>};
+    static const KernelOps k2 = {launch_fit_rw<2>, launch_batch_rw<2>, occupancy_rw<2>};
+    static const KernelOps k3 = {launch_fit_rw<3>, launch_batch_rw<3>, occupancy_rw<3>};
+    static const KernelOps k4 = {launch_fit_rw<4>, launch_batch_rw<4>, occupancy_rw<4>};
+    switch (r) {
+        case 1: return &k1;
+        case 2: return &k2;
+        case 3: return &k3;
+        case 4: return &k4;
+        default: return nullptr;
     }
 }
 

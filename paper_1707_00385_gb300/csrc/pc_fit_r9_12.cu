@@ -1,17 +1,19 @@
-// Instantiations of the fused kernel for window radii 9..12 (dense window).
+// Instantiations of the fused kernels for window radii 9..12 (dense window).
 #include "pc_fit.cuh"
 
 namespace pcurv {
 
-cudaError_t launch_fit_r9_12(const float* depth, int H, int W, const Camera& cam,
-                            const FitConfig& cfg, float* k1, float* k2, float* normal,
-                            cudaStream_t stream) {
-    switch (cfg.r) {
-        case 9: return launch_fit_rw<9>(depth, H, W, cam, cfg, k1, k2, normal, stream);
-        case 10: return launch_fit_rw<10>(depth, H, W, cam, cfg, k1, k2, normal, stream);
-        case 11: return launch_fit_rw<11>(depth, H, W, cam, cfg, k1, k2, normal, stream);
-        case 12: return launch_fit_rw<12>(depth, H, W, cam, cfg, k1, k2, normal, stream);
-        default: return cudaErrorInvalidValue;
+const KernelOps* ops_r9_12(int r) {
+    static const KernelOps k9 = {launch_fit_rw<9>, launch_batch_rw<9>, occupancy_rw<9>};
+    static const KernelOps k10 = {launch_fit_rw<10>, launch_batch_rw<10>, occupancy_rw<10>};
+    static const KernelOps k11 = {launch_fit_rw<11>, launch_batch_rw<11>, occupancy_rw<11>};
+    static const KernelOps k12 = {launch_fit_rw<12>, launch_batch_rw<12>, occupancy_rw<12>};
+    switch (r) {
+        case 9: return &k9;
+        case 10: return &k10;
+        case 11: return &k11;
+        case 12: return &k12;
+        default: return nullptr;
     }
 }
 

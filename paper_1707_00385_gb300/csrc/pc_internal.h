@@ -39,19 +39,50 @@ inline size_t fit_smem_bytes(const FitConfig& c) {
            (size_t)(TILE_H + 2 * h) * TILE_W * sizeof(int);
 }
 
-// Enqueues the fused per-pixel kernel for one H x W image on `stream`.
-// normal may be nullptr.  Returns the launch error (cudaSuccess on success).
-cudaError_t launch_fit(const float* depth, int H, int W, const Camera& cam, const FitConfig& cfg,
-                       float* k1, float* k2, float* normal, cudaStream_t stream);
+// One frame: caller-owned device buffers, size and intrinsics.
+struct FrameArgs {
+    const float* depth;
+    int H, W;
+    Camera cam;
+    float* k1;
+    float* k2;
+    float* normal;  // may be nullptr
+};
 
-// Instantiation groups (one translation unit each, compiled in parallel).
-cudaError_t launch_fit_r1_4(const float*, int, int, const Camera&, const FitConfig&, float*, float*,
-                            float*, cudaStream_t);
-cudaError_t launch_fit_r5_8(const float*, int, int, const Camera&, const FitConfig&, float*, float*,
-                            float*, cudaStream_t);
-cudaError_t launch_fit_r9_12(const float*, int, int, const Camera&, const FitConfig&, float*, float*,
-                             float*, cudaStream_t);
-cudaError_t launch_fit_generic(const float*, int, int, const Camera&, const FitConfig&, float*,
-                               float*, float*, cudaStream_t);
+// A frame of a batch and its place in the flattened tile queue.
+struct BatchFrame {
+    FrameArgs f;
+    int tiles_x;     // tiles per row of this frame
+    int tile_begin;  // first queue index of this frame
+};
+
+// Device-resident batch table: header followed by nframes descriptors.
+struct BatchTable {
+    int nframes;
+    int total_tiles;
+    int pad[2];
+    BatchFrame frames[1];  // nframes entries
+};
+
+inline size_t batch_table_bytes(int nframes) {
+    return sizeof(BatchTable) + (size_t)(nframes > 1 ? nframes - 1 : 0) * sizeof(BatchFrame);
+}
+
+// Kernel entry points of one instantiation (window radius, dense or run-time).
+struct KernelOps {
+    cudaError_t (*fit)(const FrameArgs&, const FitConfig&, cudaStream_t);
+    cudaError_t (*batch)(const BatchTable*, unsigned*, int, const FitConfig&, cudaStream_t);
+    cudaError_t (*occupancy)(const FitConfig&, int*);
+};
+
+// Instantiation groups (one translation unit each, compiled in parallel);
+// each returns its table for radius r, or nullptr.
+const KernelOps* ops_r1_4(int r);
+const KernelOps* ops_r5_8(int r);
+const KernelOps* ops_r9_12(int r);
+const KernelOps* ops_generic();
+
+// The instantiation serving cfg (dense radii 1..12 unrolled, anything else run-time).
+const KernelOps* select_ops(const FitConfig& cfg);
 
 }  // namespace pcurv

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libpcurv.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pcurv.h")
 
 PC_OK, PC_ERR_INVALID_ARG, PC_ERR_CUDA, PC_ERR_OOM, PC_ERR_TIMEOUT, PC_ERR_UNSUPPORTED = range(6)
-PC_MAX_RADIUS, PC_MAX_NORMAL_RADIUS, PC_MAX_ITERATIONS, PC_MAX_DIM = 24, 8, 64, 16384
+PC_MAX_RADIUS, PC_MAX_NORMAL_RADIUS, PC_MAX_ITERATIONS, PC_MAX_DIM, PC_MAX_BATCH = 24, 8, 64, 16384, 4096
 
 
 class pc_params(ctypes.Structure):
@@ -29,6 +29,16 @@ class pc_params(ctypes.Structure):
         ("det_tol", ctypes.c_float),
         ("pivot_tol", ctypes.c_float),
         ("min_window", ctypes.c_int),
+        ("batch_graph", ctypes.c_int),
+    ]
+
+
+class pc_frame(ctypes.Structure):
+    _fields_ = [
+        ("depth", ctypes.c_void_p),
+        ("H", ctypes.c_int), ("W", ctypes.c_int),
+        ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+        ("k1", ctypes.c_void_p), ("k2", ctypes.c_void_p), ("normal", ctypes.c_void_p),
     ]
 
 
@@ -57,12 +67,13 @@ def load() -> ctypes.CDLL:
                                                        ctypes.POINTER(pc_params), ctypes.POINTER(_vp)]
         L.pc_compute.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.pc_compute_host.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.pc_compute_batch.argtypes = [_vp, ctypes.POINTER(pc_frame), ctypes.c_int, _vp]
         L.pc_destroy.argtypes = [_vp]
         L.pc_status_string.argtypes = [ctypes.c_int]
         L.pc_status_string.restype = ctypes.c_char_p
         L.pc_last_error.argtypes = [_vp]
         L.pc_last_error.restype = ctypes.c_char_p
-        for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_destroy"):
+        for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_compute_batch", "pc_destroy"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -90,6 +101,11 @@ def pc_compute(ctx, depth, H, W, stream, k1_out, k2_out, normal_out) -> int:
 
 def pc_compute_host(ctx, depth_host, H, W, stream, k1_host, k2_host, normal_host) -> int:
     return load().pc_compute_host(ctx, depth_host, H, W, stream, k1_host, k2_host, normal_host)
+
+
+def pc_compute_batch(ctx, frames, n, stream) -> int:
+    """frames: a ctypes array of pc_frame (or None when n == 0)."""
+    return load().pc_compute_batch(ctx, frames, n, stream)
 
 
 def pc_destroy(ctx) -> int:
@@ -166,6 +182,18 @@ class Curvature:
         if st != PC_OK:
             raise PcError(st, "pc_compute", pc_last_error(self.ctx))
         return k1, k2, normal
+
+    def batch(self, frames, stream=None):
+        """pc_compute_batch over a list of (depth, (fx, fy, cx, cy), k1, k2, normal)
+        tuples of CUDA tensors (normal may be None); enqueues one persistent launch."""
+        arr = (pc_frame * max(len(frames), 1))()
+        for i, (d, intr, a, b, n) in enumerate(frames):
+            H, W = d.shape
+            arr[i] = pc_frame(d.data_ptr(), H, W, *map(float, intr), a.data_ptr(), b.data_ptr(),
+                              n.data_ptr() if n is not None else None)
+        st = pc_compute_batch(self.ctx, arr if frames else None, len(frames), _stream_handle(stream))
+        if st != PC_OK:
+            raise PcError(st, "pc_compute_batch", pc_last_error(self.ctx))
 
     def compute_host(self, depth, k1, k2, normal=None, stream=None):
         """Host-memory form (pc_compute_host): depth, k1, k2, normal are CPU

@@ -27,8 +27,8 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_destroy", "pc_status_string",
-              "pc_params_default", "pc_last_error"):
+    for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_compute_batch", "pc_destroy",
+              "pc_status_string", "pc_params_default", "pc_last_error"):
         assert f in names
 
 
@@ -48,9 +48,46 @@ def test_params_struct_matches_header(pc):
     assert all(ctype[t] is c for (t, _), (_, c) in zip(fields, pc.pc_params._fields_))
 
 
+def test_frame_struct_matches_header(pc):
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct pc_frame \{(.*?)\} pc_frame;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.replace("const ", "").strip()
+        if decl:
+            names += [n.strip().lstrip("*") for n in decl.split(None, 1)[1].split(",")]
+    names = [n.lstrip("*") for n in names]
+    assert names == [f for f, _ in pc.pc_frame._fields_]
+
+
+def test_batch_argument_checks_without_gpu(pc):
+    st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5)
+    try:
+        assert pc.pc_compute_batch(None, None, 0, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute_batch(ctx, None, 0, None) == pc.PC_OK
+        assert pc.pc_compute_batch(ctx, None, 1, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute_batch(ctx, None, -1, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute_batch(ctx, None, 4097, None) == pc.PC_ERR_INVALID_ARG
+        fr = (pc.pc_frame * 2)()
+        fr[0] = pc.pc_frame(None, 0, 0, 1.0, 1.0, 0.0, 0.0, None, None, None)      # empty: skipped
+        fr[1] = pc.pc_frame(None, 0, 10, 1.0, 1.0, 0.0, 0.0, None, None, None)
+        assert pc.pc_compute_batch(ctx, fr, 2, None) == pc.PC_OK
+        fr[1] = pc.pc_frame(None, 4, 4, 1.0, 1.0, 0.0, 0.0, None, None, None)      # NULL buffers
+        assert pc.pc_compute_batch(ctx, fr, 2, None) == pc.PC_ERR_INVALID_ARG
+        fr[1] = pc.pc_frame(None, 4, -4, 1.0, 1.0, 0.0, 0.0, None, None, None)
+        assert pc.pc_compute_batch(ctx, fr, 2, None) == pc.PC_ERR_INVALID_ARG
+        buf = (ctypes.c_float * 64)()
+        a = ctypes.addressof(buf)
+        fr[1] = pc.pc_frame(a, 4, 4, 0.0, 1.0, 0.0, 0.0, a, a, None)                # fx = 0
+        assert pc.pc_compute_batch(ctx, fr, 2, None) == pc.PC_ERR_INVALID_ARG
+    finally:
+        pc.pc_destroy(ctx)
+
+
 def test_limits_match_header(pc):
     text = open(HEADER).read()
-    for name in ("PC_MAX_RADIUS", "PC_MAX_NORMAL_RADIUS", "PC_MAX_ITERATIONS", "PC_MAX_DIM"):
+    for name in ("PC_MAX_RADIUS", "PC_MAX_NORMAL_RADIUS", "PC_MAX_ITERATIONS", "PC_MAX_DIM", "PC_MAX_BATCH"):
         val = int(re.search(rf"#define {name} (\d+)", text).group(1))
         assert getattr(pc.pcurv, name) == val
 
@@ -60,6 +97,7 @@ def test_defaults(pc):
     assert p.k == pytest.approx(1e-4) and p.reject == 0 and p.reject_ratio == 2.0
     assert p.normal_radius == 3 and p.stride == 1 and p.min_window == 6
     assert p.pivot_tol == pytest.approx(1e-5) and p.det_tol == pytest.approx(1e-6)
+    assert p.batch_graph == 1
 
 
 def test_status_strings(pc):
@@ -82,7 +120,8 @@ def test_create_rejects_bad_arguments(pc, args):
 @pytest.mark.parametrize("field,value", [("k", 0.0), ("k", float("nan")), ("reject", 2),
                                          ("reject_ratio", 0.0), ("normal_radius", 0),
                                          ("normal_radius", 9), ("stride", 0), ("min_window", 5),
-                                         ("pivot_tol", -1.0), ("det_tol", float("inf"))])
+                                         ("pivot_tol", -1.0), ("det_tol", float("inf")),
+                                         ("batch_graph", 2)])
 def test_create_rejects_bad_params(pc, field, value):
     p = pc.pc_params_default()
     setattr(p, field, value)

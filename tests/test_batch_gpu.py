@@ -1,0 +1,140 @@
+"""pc_compute_batch: uneven frames in one persistent launch over a flattened
+tile queue equal pc_compute frame by frame, bit for bit, with and without
+the CUDA graph, across repeated calls and capacity growth."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_00385_gb300 import build
+    build.build()
+    import paper_1707_00385_gb300 as pc
+    pc.load()
+    return pc
+
+
+SIZES = [(240, 320), (424, 512), (480, 640), (720, 1280), (37, 45), (8, 32), (1, 1)]
+
+
+@pytest.fixture(scope="module")
+def frames():
+    out = []
+    for i, (H, W) in enumerate(SIZES * 2):
+        s = synth.kinect_scene(100 + i, H=H, W=W, noise="tof" if (H, W) == (424, 512) else "kinect",
+                               nprims=6) if H >= 100 else \
+            synth.crop(synth.kinect_scene(100 + i), 200, 300, H, W)
+        out.append(s)
+    return out
+
+
+def per_frame(pc, scenes, r, T, **kw):
+    import torch
+    res = []
+    for s in scenes:
+        c = pc.Curvature(*s.intrinsics, window_radius=r, iterations=T, **kw)
+        k1, k2, n = c(torch.from_numpy(s.depth).cuda())
+        torch.cuda.synchronize()
+        res.append((k1.cpu().numpy(), k2.cpu().numpy(), n.cpu().numpy()))
+        c.close()
+    return res
+
+
+def batched(pc, c, scenes, with_normal=True):
+    import torch
+    args, outs = [], []
+    for s in scenes:
+        d = torch.from_numpy(s.depth).cuda()
+        k1, k2 = torch.full(d.shape, 5.0, device="cuda"), torch.full(d.shape, 5.0, device="cuda")
+        n = torch.full(d.shape + (3,), 5.0, device="cuda") if with_normal else None
+        args.append((d, s.intrinsics, k1, k2, n))
+        outs.append((k1, k2, n))
+    c.batch(args)
+    torch.cuda.synchronize()
+    return [(a.cpu().numpy(), b.cpu().numpy(), n.cpu().numpy() if n is not None else None)
+            for a, b, n in outs]
+
+
+def same(a, b):
+    return np.array_equal(a, b, equal_nan=True)
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+def test_batch_equals_per_frame(gpu, frames, graph):
+    ref = per_frame(gpu, frames, 7, 5)
+    c = gpu.Curvature(525.0, 525.0, 0.0, 0.0, window_radius=7, iterations=5, batch_graph=graph)
+    got = batched(gpu, c, frames)
+    c.close()
+    for (a1, a2, an), (b1, b2, bn) in zip(ref, got):
+        assert same(a1, b1) and same(a2, b2) and same(an, bn)
+
+
+def test_repeated_calls_growth_and_alternation(gpu, frames):
+    """Several calls in a row on one context: small, large (capacity grows,
+    graphs are recaptured), small again; both staging copies get reused."""
+    import torch
+    ref = per_frame(gpu, frames, 5, 3)
+    c = gpu.Curvature(525.0, 525.0, 0.0, 0.0, window_radius=5, iterations=3)
+    plan = [frames[:3], frames, frames[3:6], frames[:1], frames[2:14], frames[:3]]
+    idx = [list(range(3)), list(range(len(frames))), [3, 4, 5], [0], list(range(2, 14)), [0, 1, 2]]
+    for sel, ids in zip(plan, idx):
+        got = batched(gpu, c, sel)
+        for i, (b1, b2, bn) in zip(ids, got):
+            a1, a2, an = ref[i]
+            assert same(a1, b1) and same(a2, b2) and same(an, bn)
+    c.close()
+    torch.cuda.synchronize()
+
+
+def test_batch_skips_empty_frames_and_normals_optional(gpu, frames):
+    import torch
+    c = gpu.Curvature(525.0, 525.0, 0.0, 0.0, window_radius=3, iterations=2)
+    ref = per_frame(gpu, frames[:3], 3, 2)
+    empty = torch.zeros((0, 7), device="cuda")
+    e1, e2 = torch.zeros((0, 7), device="cuda"), torch.zeros((0, 7), device="cuda")
+    args = []
+    outs = []
+    for s in frames[:3]:
+        d = torch.from_numpy(s.depth).cuda()
+        k1, k2 = torch.empty(d.shape, device="cuda"), torch.empty(d.shape, device="cuda")
+        args.append((d, s.intrinsics, k1, k2, None))
+        outs.append((k1, k2))
+        args.append((empty, (1.0, 1.0, 0.0, 0.0), e1, e2, None))
+    c.batch(args)
+    torch.cuda.synchronize()
+    for (k1, k2), (a1, a2, _) in zip(outs, ref):
+        assert same(k1.cpu().numpy(), a1) and same(k2.cpu().numpy(), a2)
+    c.batch([])   # nothing to do
+    c.close()
+
+
+def test_batch_runtime_radius_and_stride(gpu, frames):
+    sel = [frames[0], frames[4], frames[1]]
+    for kw in ({"window_radius": 15}, {"window_radius": 9, "stride": 3}):
+        r = kw.pop("window_radius")
+        ref = per_frame(gpu, sel, r, 3, **kw)
+        c = gpu.Curvature(525.0, 525.0, 0.0, 0.0, window_radius=r, iterations=3, **kw)
+        got = batched(gpu, c, sel)
+        c.close()
+        for (a1, a2, an), (b1, b2, bn) in zip(ref, got):
+            assert same(a1, b1) and same(a2, b2) and same(an, bn)
+
+
+def test_batched_frame_against_oracle(gpu, orc, frames):
+    """One frame of a batch checked directly against the oracle."""
+    from oracle import parity
+    s = synth.crop(frames[2], 150, 250, 60, 90)
+    c = gpu.Curvature(*s.intrinsics, window_radius=7, iterations=5)
+    (k1, k2, n), = batched(gpu, c, [s])
+    c.close()
+    ref = parity.reference(s.depth, orc.params(*s.intrinsics, r=7, T=5, pivot_tol=1e-5))
+    rep = parity.compare(k1, k2, n, ref, pivot_tol=1e-5)
+    assert rep.ok() and rep.n_well_posed > 0.3 * rep.n_valid_oracle, rep.summary()
+    assert rep.frac_within_tol_all > 0.9, rep.summary()
