@@ -138,6 +138,28 @@ typedef struct pc_frame {
  * between, because the device scratch is shared. */
 pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream);
 
+/* pc_compute_batch for callers that cannot allocate device memory.  Some
+ * host programs own every byte of device memory themselves (a framework's
+ * pool whose accounting must stay exact, or a fixed budget reserved at
+ * start-up), and latency-bound loops cannot afford cudaMalloc, which can wait
+ * for the whole device.  This entry point allocates nothing: its scratch (the
+ * tile counter and a frame table of at most PC_STATIC_MAX_FRAMES frames) is a
+ * fixed array inside the library (about 19 KB, held on every GPU that loads
+ * the library until the process exits), and the frame table is staged
+ * through a fixed host array.  The paper has no counterpart; the results equal
+ * pc_compute_batch bit for bit.
+ *   - n > PC_STATIC_MAX_FRAMES is rejected with PC_ERR_INVALID_ARG (message
+ *     in pc_last_error); other arguments as for pc_compute_batch.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - Every call uses the same array (the counter is cleared by each call, the
+ *     table overwritten), so calls that overlap on the GPU -- on different
+ *     streams or from different threads -- race: keep them on one stream or
+ *     synchronise in between. */
+#define PC_STATIC_MAX_FRAMES 256
+pc_status pc_compute_batch_static(pc_ctx* ctx, const pc_frame* frames, int n, void* stream);
+
 /* Frees the context, its staging buffers, batch scratch and graphs
  * (synchronising the device first when it owns any).  NULL is a no-op
  * returning PC_OK. */

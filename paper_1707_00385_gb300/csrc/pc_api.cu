@@ -144,6 +144,12 @@ const KernelOps* select_ops(const FitConfig& cfg) {
     return k ? k : ops_generic();
 }
 
+const FitConfig& ctx_config(const pc_ctx* ctx) { return ctx->cfg; }
+
+void ctx_set_error(pc_ctx* ctx, const char* msg) {
+    if (ctx) snprintf(ctx->last_error, sizeof ctx->last_error, "%s", msg);
+}
+
 }  // namespace pcurv
 
 extern "C" {

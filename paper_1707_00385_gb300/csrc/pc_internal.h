@@ -86,3 +86,14 @@ const KernelOps* ops_generic();
 const KernelOps* select_ops(const FitConfig& cfg);
 
 }  // namespace pcurv
+
+struct pc_ctx;
+
+namespace pcurv {
+
+// Read access to a context's kernel parameters, and a way to leave a message
+// for pc_last_error(), for entry points defined outside pc_api.cu.
+const FitConfig& ctx_config(const pc_ctx* ctx);
+void ctx_set_error(pc_ctx* ctx, const char* msg);
+
+}  // namespace pcurv

@@ -17,6 +17,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "pcurv.h")
 
 PC_OK, PC_ERR_INVALID_ARG, PC_ERR_CUDA, PC_ERR_OOM, PC_ERR_TIMEOUT, PC_ERR_UNSUPPORTED = range(6)
 PC_MAX_RADIUS, PC_MAX_NORMAL_RADIUS, PC_MAX_ITERATIONS, PC_MAX_DIM, PC_MAX_BATCH = 24, 8, 64, 16384, 4096
+PC_STATIC_MAX_FRAMES = 256
 
 
 class pc_params(ctypes.Structure):
@@ -68,12 +69,14 @@ def load() -> ctypes.CDLL:
         L.pc_compute.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.pc_compute_host.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.pc_compute_batch.argtypes = [_vp, ctypes.POINTER(pc_frame), ctypes.c_int, _vp]
+        L.pc_compute_batch_static.argtypes = [_vp, ctypes.POINTER(pc_frame), ctypes.c_int, _vp]
         L.pc_destroy.argtypes = [_vp]
         L.pc_status_string.argtypes = [ctypes.c_int]
         L.pc_status_string.restype = ctypes.c_char_p
         L.pc_last_error.argtypes = [_vp]
         L.pc_last_error.restype = ctypes.c_char_p
-        for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_compute_batch", "pc_destroy"):
+        for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_compute_batch",
+                  "pc_compute_batch_static", "pc_destroy"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -106,6 +109,11 @@ def pc_compute_host(ctx, depth_host, H, W, stream, k1_host, k2_host, normal_host
 def pc_compute_batch(ctx, frames, n, stream) -> int:
     """frames: a ctypes array of pc_frame (or None when n == 0)."""
     return load().pc_compute_batch(ctx, frames, n, stream)
+
+
+def pc_compute_batch_static(ctx, frames, n, stream) -> int:
+    """The batch entry point that allocates no device memory (fixed scratch)."""
+    return load().pc_compute_batch_static(ctx, frames, n, stream)
 
 
 def pc_destroy(ctx) -> int:

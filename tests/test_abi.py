@@ -87,7 +87,8 @@ def test_batch_argument_checks_without_gpu(pc):
 
 def test_limits_match_header(pc):
     text = open(HEADER).read()
-    for name in ("PC_MAX_RADIUS", "PC_MAX_NORMAL_RADIUS", "PC_MAX_ITERATIONS", "PC_MAX_DIM", "PC_MAX_BATCH"):
+    for name in ("PC_MAX_RADIUS", "PC_MAX_NORMAL_RADIUS", "PC_MAX_ITERATIONS", "PC_MAX_DIM", "PC_MAX_BATCH",
+                 "PC_STATIC_MAX_FRAMES"):
         val = int(re.search(rf"#define {name} (\d+)", text).group(1))
         assert getattr(pc.pcurv, name) == val
 
