@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--scenes", type=int, default=SCENES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--report", choices=["precision"], default=None,
+                    help="instead of the benchmark line, print the error of each precision variant "
+                         "against the FP64 oracle (one 640x480 frame, radii 3, 7, 11)")
     return ap.parse_args()
 
 
@@ -226,8 +229,63 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def precision_report(args):
+    """Error of each precision variant against the FP64 oracle on one seeded
+    640x480 Kinect-like frame, per window radius, with its time per frame."""
+    import torch
+    import oracle
+    import paper_1707_00385_gb300 as pc
+    from paper_1707_00385_gb300 import build as pcbuild
+    pcbuild.build()
+    s = scenes(1)[0]
+    intr = s.intrinsics
+    d = torch.from_numpy(s.depth).cuda()
+    variants = [("fp32", {}, 0), ("fp32_kahan", {"kahan": 1}, 0),
+                ("fp32_fp64solve", {"pivot_tol": 1e-7, "fp64_solve_cond": 1e6}, 0),
+                ("fp16_storage", {}, 1), ("bf16_storage", {}, 2)]
+    rows = []
+    for r in (3, 7, 11):
+        ref = {}
+        for name, kw, fmt in variants:
+            piv = kw.get("pivot_tol", 1e-5)
+            if piv not in ref:
+                ref[piv] = oracle.curvature_image(s.depth, oracle.params(*intr, r=r, T=ITERS, pivot_tol=piv))
+            f = ref[piv]
+            c = pc.Curvature(*intr, window_radius=r, iterations=ITERS, **kw)
+            if fmt:
+                packed, base = c.pack(d, fmt)
+                run = lambda: c.compute_packed(packed, base, fmt)
+            else:
+                run = lambda: c(d)
+            for _ in range(3):
+                out = run()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                out = run()
+            e1.record()
+            torch.cuda.synchronize()
+            k1, k2 = out[0].cpu().numpy(), out[1].cpu().numpy()
+            c.close()
+            ok = f.status == oracle.OK
+            both = ok & np.isfinite(k1)
+            err = np.maximum(np.abs(k1 - f.k1), np.abs(k2 - f.k2))[both]
+            rel = np.maximum(np.abs(k1 - f.k1) / (1e-4 + 1e-4 * np.abs(f.k1)),
+                             np.abs(k2 - f.k2) / (1e-4 + 1e-4 * np.abs(f.k2)))[both]
+            rows.append({"variant": name, "window_radius": r, "ms_per_frame": e0.elapsed_time(e1) / 10,
+                         "valid_both": int(both.sum()), "validity_mismatch": int(np.sum(ok != np.isfinite(k1))),
+                         "median_abs_dk": float(np.median(err)), "p99_abs_dk": float(np.quantile(err, 0.99)),
+                         "frac_within_tol": float(np.mean(rel <= 1))})
+            print(json.dumps(rows[-1]), flush=True)
+    return rows
+
+
 def main():
     args = parse()
+    if args.report == "precision":
+        precision_report(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

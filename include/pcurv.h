@@ -85,6 +85,12 @@ typedef struct pc_params {
     int batch_graph;     /* 1 = pc_compute_batch replays a CUDA graph (copy of the frame table,
                             reset of the tile queue, persistent kernel) captured once per
                             table capacity; 0 = enqueue the three steps directly. Default 1 */
+    int kahan;           /* 1 = compensated (Kahan) summation of the window moments in FP32;
+                            costs about 2.3x the time of plain sums. Default 0 */
+    float fp64_solve_cond; /* > 0: when the scaled condition estimate of the re-weighted system
+                            (1 / smallest scaled pivot) exceeds this value, the 6x6 system is
+                            factorised again in FP64 and singularity is judged on the FP64
+                            pivots. 0 = off (default) */
 } pc_params;
 
 /* Writes the defaults above into *p (no-op for NULL). */
@@ -114,6 +120,31 @@ pc_status pc_compute(pc_ctx* ctx, const float* depth, int H, int W, void* stream
  * calls on one ctx must use one stream, or synchronise in between. */
 pc_status pc_compute_host(pc_ctx* ctx, const float* depth_host, int H, int W, void* stream,
                           float* k1_host, float* k2_host, float* normal_host);
+
+/* Range storage formats of pc_pack_depth / pc_compute_packed. */
+#define PC_DEPTH_F16 1           /* IEEE half offsets from a per-tile FP32 base */
+#define PC_DEPTH_BF16 2          /* bfloat16 offsets from a per-tile FP32 base */
+#define PC_PACK_TILE_W 32        /* pixels per storage tile: 32 columns x 8 rows */
+#define PC_PACK_TILE_H 8
+
+/* Packs a float32 range image into centred 16-bit storage: for each 32x8
+ * tile (row-major over ceil(W/32) x ceil(H/8) tiles) one FP32 base, the
+ * midpoint of its valid ranges, and per pixel the offset (range - base)
+ * rounded to the nearest FP16 or BF16 value (format PC_DEPTH_F16 or
+ * PC_DEPTH_BF16).  Pixels without a valid range store NaN.
+ *   depth     device, H*W floats
+ *   packed    device, H*W 16-bit values (2-byte aligned)
+ *   tile_base device, ceil(W/32)*ceil(H/8) floats */
+pc_status pc_pack_depth(pc_ctx* ctx, const float* depth, int H, int W, int format, void* stream,
+                        unsigned short* packed, float* tile_base);
+
+/* pc_compute reading the packed storage of pc_pack_depth (range = base +
+ * offset, in FP32).  The arithmetic after loading is that of pc_compute; the
+ * storage rounding is the only difference (its error against the FP64 oracle
+ * is measured, not bounded by the FP32 tolerance). */
+pc_status pc_compute_packed(pc_ctx* ctx, const unsigned short* packed, const float* tile_base,
+                            int format, int H, int W, void* stream, float* k1_out, float* k2_out,
+                            float* normal_out);
 
 /* One frame of a batch: its own size, intrinsics (pixels) and device buffers,
  * with the layouts of pc_compute. */

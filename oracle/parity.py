@@ -20,8 +20,10 @@ of the tolerance is not determined to that tolerance at single precision.
 Every other pixel ("well-posed") must be within tolerance.
 
 Validity (NaN or not) must agree except where the oracle's smallest scaled
-pivot lies within a factor `band` of the singularity threshold, where the
-decision itself is below single-precision resolution.
+pivot lies within a factor `band` of the singularity threshold (or of
+`pivot_resolution`, the smallest pivot the implementation's sums resolve,
+when that is larger), where the decision itself is below the
+implementation's resolution.
 """
 from __future__ import annotations
 
@@ -97,7 +99,8 @@ class Report:
                 f"{self.max_normal_angle_well_posed:.3g} rad")
 
 
-def compare(k1, k2, normal, ref: Reference, pivot_tol: float, band: float = 10.0) -> Report:
+def compare(k1, k2, normal, ref: Reference, pivot_tol: float, band: float = 10.0,
+            pivot_resolution: float = 0.0) -> Report:
     f = ref.field
     k1, k2 = np.asarray(k1, np.float64), np.asarray(k2, np.float64)
     g_valid = np.isfinite(k1)
@@ -107,7 +110,7 @@ def compare(k1, k2, normal, ref: Reference, pivot_tol: float, band: float = 10.0
         nan_ok = nan_ok and bool(np.array_equal(g_valid, np.isfinite(normal).all(-1)))
     o_valid = f.status == OK
     near = ((f.status == OK) | (f.status == SINGULAR)) & (f.min_pivot >= pivot_tol / band) & \
-           (f.min_pivot <= pivot_tol * band)
+           (f.min_pivot <= max(pivot_tol, pivot_resolution) * band)
     near |= f.status == BAD_NORMAL  # the 2x2 degeneracy test has no pivot record; counted as band
     mism = o_valid != g_valid
     both = o_valid & g_valid

@@ -79,6 +79,8 @@ pc_status check_params(const pc_params& p) {
     if (!(finite_f(p.pivot_tol) && p.pivot_tol >= 0.f)) return PC_ERR_INVALID_ARG;
     if (p.min_window < 6) return PC_ERR_INVALID_ARG;  // six parameters need six points
     if (p.batch_graph != 0 && p.batch_graph != 1) return PC_ERR_INVALID_ARG;
+    if (p.kahan != 0 && p.kahan != 1) return PC_ERR_INVALID_ARG;
+    if (!(finite_f(p.fp64_solve_cond) && p.fp64_solve_cond >= 0.f)) return PC_ERR_INVALID_ARG;
     return PC_OK;
 }
 
@@ -135,6 +137,7 @@ int round_up_pow2(int n) {
 namespace pcurv {
 
 const KernelOps* select_ops(const FitConfig& cfg) {
+    if (cfg.kahan) return ops_precision(1, 0);
     const KernelOps* k = nullptr;
     if (cfg.stride == 1) {
         if (cfg.r >= 1 && cfg.r <= 4) k = ops_r1_4(cfg.r);
@@ -165,6 +168,8 @@ void pc_params_default(pc_params* p) {
     p->pivot_tol = 1e-5f;
     p->min_window = 6;
     p->batch_graph = 1;
+    p->kahan = 0;
+    p->fp64_solve_cond = 0.f;
 }
 
 pc_status pc_create(float fx, float fy, float cx, float cy, int window_radius, int iterations,
@@ -184,7 +189,8 @@ pc_status pc_create(float fx, float fy, float cx, float cy, int window_radius, i
     c->params = p;
     c->cam = pcurv::Camera{fx, fy, cx, cy, 1.f / fx, 1.f / fy};
     c->cfg = pcurv::FitConfig{window_radius, p.normal_radius, iterations, p.stride, 1.f / p.k,
-                              p.reject, p.reject_ratio, p.det_tol, p.pivot_tol, p.min_window};
+                              p.reject, p.reject_ratio, p.det_tol, p.pivot_tol, p.min_window,
+                              p.kahan, p.fp64_solve_cond > 0.f ? 1.f / p.fp64_solve_cond : 0.f};
     *out = c;
     return PC_OK;
 }
@@ -196,9 +202,45 @@ pc_status pc_compute(pc_ctx* ctx, const float* depth, int H, int W, void* stream
     if (st != PC_OK) return st;
     if (H == 0 || W == 0) return PC_OK;
     if ((st = check_buffers(depth, k1_out, k2_out, normal_out)) != PC_OK) return st;
-    const pcurv::FrameArgs f{depth, H, W, ctx->cam, k1_out, k2_out, normal_out};
+    const pcurv::FrameArgs f{depth, H, W, ctx->cam, k1_out, k2_out, normal_out, nullptr, nullptr};
     const cudaError_t e = pcurv::select_ops(ctx->cfg)->fit(f, ctx->cfg, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute launch");
+    return PC_OK;
+}
+
+static bool aligned2(const void* p) { return ((uintptr_t)p & 1u) == 0; }
+
+pc_status pc_pack_depth(pc_ctx* ctx, const float* depth, int H, int W, int format, void* stream,
+                        unsigned short* packed, float* tile_base) {
+    if (!ctx || (format != PC_DEPTH_F16 && format != PC_DEPTH_BF16)) return PC_ERR_INVALID_ARG;
+    pc_status st = check_image(H, W);
+    if (st != PC_OK) return st;
+    if (H == 0 || W == 0) return PC_OK;
+    if (!depth || !packed || !tile_base || !aligned4(depth) || !aligned2(packed) || !aligned4(tile_base))
+        return PC_ERR_INVALID_ARG;
+    if (!is_device_ptr(depth) || !is_device_ptr(packed) || !is_device_ptr(tile_base))
+        return PC_ERR_INVALID_ARG;
+    const cudaError_t e = pcurv::launch_pack(depth, H, W, format, packed, tile_base, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_pack_depth launch");
+    return PC_OK;
+}
+
+pc_status pc_compute_packed(pc_ctx* ctx, const unsigned short* packed, const float* tile_base, int format,
+                            int H, int W, void* stream, float* k1_out, float* k2_out, float* normal_out) {
+    if (!ctx || (format != PC_DEPTH_F16 && format != PC_DEPTH_BF16)) return PC_ERR_INVALID_ARG;
+    pc_status st = check_image(H, W);
+    if (st != PC_OK) return st;
+    if (H == 0 || W == 0) return PC_OK;
+    if (!packed || !tile_base || !aligned2(packed) || !aligned4(tile_base) || !is_device_ptr(packed) ||
+        !is_device_ptr(tile_base))
+        return PC_ERR_INVALID_ARG;
+    if (!k1_out || !k2_out || !aligned4(k1_out) || !aligned4(k2_out) || !aligned4(normal_out) ||
+        !is_device_ptr(k1_out) || !is_device_ptr(k2_out) || (normal_out && !is_device_ptr(normal_out)))
+        return PC_ERR_INVALID_ARG;
+    const pcurv::FrameArgs f{nullptr, H, W, ctx->cam, k1_out, k2_out, normal_out, packed, tile_base};
+    const cudaError_t e =
+        pcurv::ops_precision(ctx->cfg.kahan, format)->fit(f, ctx->cfg, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_packed launch");
     return PC_OK;
 }
 
@@ -244,7 +286,7 @@ pc_status pc_compute_host(pc_ctx* ctx, const float* depth_host, int H, int W, vo
                              s)) != cudaSuccess)
         return cuda_fail(ctx, e, "depth H2D");
     const pcurv::FrameArgs f{ctx->d_depth, H, W, ctx->cam, ctx->d_k1, ctx->d_k2,
-                             normal_host ? ctx->d_normal : nullptr};
+                             normal_host ? ctx->d_normal : nullptr, nullptr, nullptr};
     e = pcurv::select_ops(ctx->cfg)->fit(f, ctx->cfg, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_host launch");
     if ((e = cudaMemcpyAsync(k1_host, ctx->d_k1, npx * sizeof(float), cudaMemcpyDeviceToHost, s)) !=
@@ -361,7 +403,7 @@ pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* str
         pcurv::BatchFrame& d = t->frames[k++];
         d.f = pcurv::FrameArgs{fr.depth, fr.H, fr.W,
                                pcurv::Camera{fr.fx, fr.fy, fr.cx, fr.cy, 1.f / fr.fx, 1.f / fr.fy},
-                               fr.k1, fr.k2, fr.normal};
+                               fr.k1, fr.k2, fr.normal, nullptr, nullptr};
         d.tiles_x = (fr.W + pcurv::TILE_W - 1) / pcurv::TILE_W;
         d.tile_begin = begin;
         begin += d.tiles_x * ((fr.H + pcurv::TILE_H - 1) / pcurv::TILE_H);

@@ -42,6 +42,9 @@
 #include <cfloat>
 #include <cuda_runtime.h>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "pc_f32x2.cuh"
 #include "pc_internal.h"
 
@@ -108,11 +111,45 @@ __device__ __forceinline__ void local_xyz2(const Coef2& k, f32x2 Z, f32x2 DU, f3
     Hh = fma2(fma2(DU, k.cx2, RH), Z, mul2(k.bh, dZ));
 }
 
+// Precision variants of the kernels (template parameter PREC): bit 0 selects
+// compensated sums, bits 1-2 the range storage (0 float32, 1 FP16 offsets,
+// 2 BF16 offsets from a per-tile base).
+constexpr int PREC_KAHAN = 1;
+__host__ __device__ constexpr int prec_format(int prec) { return prec >> 1; }
+
+// sum += a * b, plain or compensated.  The compensated form (Kahan) keeps
+// nc = -(rounding error so far): y = a b - c, t = s + y, c' = (t - s) - y.
+template <bool KAHAN>
+__device__ __forceinline__ void acc_fma(f32x2& s, f32x2& nc, f32x2 a, f32x2 b) {
+    if (KAHAN) {
+        const f32x2 y = fma2(a, b, nc);
+        const f32x2 t = add2(s, y);
+        nc = sub2(y, sub2(t, s));
+        s = t;
+    } else {
+        s = fma2(a, b, s);
+    }
+}
+
+template <bool KAHAN>
+__device__ __forceinline__ void acc_add(f32x2& s, f32x2& nc, f32x2 x) {
+    if (KAHAN) {
+        const f32x2 y = add2(x, nc);
+        const f32x2 t = add2(s, y);
+        nc = sub2(y, sub2(t, s));
+        s = t;
+    } else {
+        s = add2(s, x);
+    }
+}
+
 // One symmetric pair: residuals (Eq. quad in the local frame), weights,
 // Jacobian rows and the 26 sums.  C = (c_a, c_b), 1 valid / +inf invalid.
-template <bool REJECT>
-__device__ __forceinline__ void visit2(Moments2& m, const Coef2& k, float za, float zb, float ca,
-                                       float cb, f32x2 DU, f32x2 RX, f32x2 RY, f32x2 RH, float thr) {
+// c holds the compensations of the sums when KAHAN (unused otherwise).
+template <bool REJECT, bool KAHAN>
+__device__ __forceinline__ void visit2(Moments2& m, Moments2& c, const Coef2& k, float za, float zb,
+                                       float ca, float cb, f32x2 DU, f32x2 RX, f32x2 RY, f32x2 RH,
+                                       float thr) {
     const f32x2 Z = pack(za, zb);
     f32x2 X, Y, Hh;
     local_xyz2(k, Z, DU, RX, RY, RH, X, Y, Hh);
@@ -135,32 +172,32 @@ __device__ __forceinline__ void visit2(Moments2& m, const Coef2& k, float za, fl
     const f32x2 J1 = fma2(fma2(k.A, X, mul2(k.B, Y)), Hh, X);
     const f32x2 WE = mul2(Wt, EPS), WJ0 = mul2(Wt, NJ0), WJ1 = mul2(Wt, J1);
     const f32x2 WXX = mul2(Wt, XX), WXY = mul2(Wt, XY), WYY = mul2(Wt, YY);
-    m.h00 = fma2(WJ0, NJ0, m.h00);
-    m.h01 = fma2(WJ0, J1, m.h01);
-    m.h11 = fma2(WJ1, J1, m.h11);
-    m.s0 = add2(m.s0, WJ0);
-    m.s1 = add2(m.s1, WJ1);
-    m.h03 = fma2(WJ0, XX, m.h03);
-    m.h04 = fma2(WJ0, XY, m.h04);
-    m.h05 = fma2(WJ0, YY, m.h05);
-    m.h13 = fma2(WJ1, XX, m.h13);
-    m.h14 = fma2(WJ1, XY, m.h14);
-    m.h15 = fma2(WJ1, YY, m.h15);
-    m.sw = add2(m.sw, Wt);
-    m.sxx = add2(m.sxx, WXX);
-    m.sxy = add2(m.sxy, WXY);
-    m.syy = add2(m.syy, WYY);
-    m.m40 = fma2(WXX, XX, m.m40);
-    m.m31 = fma2(WXX, XY, m.m31);
-    m.m22 = fma2(WXX, YY, m.m22);
-    m.m13 = fma2(WXY, YY, m.m13);
-    m.m04 = fma2(WYY, YY, m.m04);
-    m.g0 = fma2(WE, NJ0, m.g0);
-    m.g1 = fma2(WE, J1, m.g1);
-    m.ge = add2(m.ge, WE);
-    m.g3 = fma2(WE, XX, m.g3);
-    m.g4 = fma2(WE, XY, m.g4);
-    m.g5 = fma2(WE, YY, m.g5);
+    acc_fma<KAHAN>(m.h00, c.h00, WJ0, NJ0);
+    acc_fma<KAHAN>(m.h01, c.h01, WJ0, J1);
+    acc_fma<KAHAN>(m.h11, c.h11, WJ1, J1);
+    acc_add<KAHAN>(m.s0, c.s0, WJ0);
+    acc_add<KAHAN>(m.s1, c.s1, WJ1);
+    acc_fma<KAHAN>(m.h03, c.h03, WJ0, XX);
+    acc_fma<KAHAN>(m.h04, c.h04, WJ0, XY);
+    acc_fma<KAHAN>(m.h05, c.h05, WJ0, YY);
+    acc_fma<KAHAN>(m.h13, c.h13, WJ1, XX);
+    acc_fma<KAHAN>(m.h14, c.h14, WJ1, XY);
+    acc_fma<KAHAN>(m.h15, c.h15, WJ1, YY);
+    acc_add<KAHAN>(m.sw, c.sw, Wt);
+    acc_add<KAHAN>(m.sxx, c.sxx, WXX);
+    acc_add<KAHAN>(m.sxy, c.sxy, WXY);
+    acc_add<KAHAN>(m.syy, c.syy, WYY);
+    acc_fma<KAHAN>(m.m40, c.m40, WXX, XX);
+    acc_fma<KAHAN>(m.m31, c.m31, WXX, XY);
+    acc_fma<KAHAN>(m.m22, c.m22, WXX, YY);
+    acc_fma<KAHAN>(m.m13, c.m13, WXY, YY);
+    acc_fma<KAHAN>(m.m04, c.m04, WYY, YY);
+    acc_fma<KAHAN>(m.g0, c.g0, WE, NJ0);
+    acc_fma<KAHAN>(m.g1, c.g1, WE, J1);
+    acc_add<KAHAN>(m.ge, c.ge, WE);
+    acc_fma<KAHAN>(m.g3, c.g3, WE, XX);
+    acc_fma<KAHAN>(m.g4, c.g4, WE, XY);
+    acc_fma<KAHAN>(m.g5, c.g5, WE, YY);
 }
 
 // Squared residuals of a pair, 0 for invalid points (rejection pre-pass).
@@ -174,22 +211,83 @@ __device__ __forceinline__ float sq_residual2(const Coef2& k, float za, float zb
     return (ca == 1.f ? ea : 0.f) + (cb == 1.f ? eb : 0.f);
 }
 
-// Solves (J^T W J) b = J^T W eps from the 26 sums, b returned as the update
-// delta = -b.  Jacobi-scaled LDL^T: S = D H D, D = diag(H)^-1/2; singular when
-// a diagonal entry is <= 0 or a pivot of S is <= pivot_tol.
-__device__ __forceinline__ bool solve_update(const Moments2& m, float wc, float ec, float pivot_tol,
-                                             float delta[6]) {
-    // fold the pairs; the centre point adds w_c to sum w and w_c eps_c to sum w eps
-    const float h00 = hsum(m.h00), h01 = -hsum(m.h01), h11 = hsum(m.h11);
-    const float s0 = hsum(m.s0), s1 = hsum(m.s1);
-    const float h03 = -hsum(m.h03), h04 = -hsum(m.h04), h05 = -hsum(m.h05);
-    const float h13 = hsum(m.h13), h14 = hsum(m.h14), h15 = hsum(m.h15);
-    const float sw = hsum(m.sw) + wc;
-    const float sxx = hsum(m.sxx), sxy = hsum(m.sxy), syy = hsum(m.syy);
-    const float m40 = hsum(m.m40), m31 = hsum(m.m31), m22 = hsum(m.m22), m13 = hsum(m.m13),
-                m04 = hsum(m.m04);
-    const float g0 = -hsum(m.g0), g1 = hsum(m.g1), ge = fmaf(wc, ec, hsum(m.ge));
-    const float g3 = hsum(m.g3), g4 = hsum(m.g4), g5 = hsum(m.g5);
+// Jacobi-scaled LDL^T solve of H b = g (H symmetric, upper triangle used),
+// returning delta = -b and the smallest scaled pivot.  T is float or double.
+template <typename T>
+__device__ __forceinline__ void ldlt6(const T (&H)[6][6], const T (&g)[6], T delta[6], T& min_pivot,
+                                      bool& positive_diag) {
+    T D[6];
+    positive_diag = true;
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        positive_diag = positive_diag && (H[i][i] > T(0));
+        D[i] = T(1) / sqrt(H[i][i] > T(0) ? H[i][i] : T(1));
+    }
+    T S[6][6], L[6][6], d[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++)
+#pragma unroll
+        for (int j = i; j < 6; j++) S[i][j] = H[i][j] * D[i] * D[j];
+    min_pivot = T(1);
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        T dj = S[j][j];
+#pragma unroll
+        for (int k = 0; k < j; k++) dj -= L[j][k] * L[j][k] * d[k];
+        min_pivot = dj < min_pivot ? dj : min_pivot;
+        min_pivot = dj == dj ? min_pivot : T(-1);  // NaN counts as singular
+        d[j] = dj;
+        const T idj = T(1) / dj;
+#pragma unroll
+        for (int i = j + 1; i < 6; i++) {
+            T s = S[j][i];
+#pragma unroll
+            for (int k = 0; k < j; k++) s -= L[i][k] * L[j][k] * d[k];
+            L[i][j] = s * idj;
+        }
+    }
+    T z[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        T s = D[i] * g[i];
+#pragma unroll
+        for (int k = 0; k < i; k++) s -= L[i][k] * z[k];
+        z[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; i++) z[i] /= d[i];
+#pragma unroll
+    for (int i = 5; i >= 0; i--) {
+        T s = z[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; k++) s -= L[k][i] * z[k];
+        z[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; i++) delta[i] = -D[i] * z[i];
+}
+
+// Folds the 26 pairs (with their compensations when KAHAN), adds the centre
+// point (w_c to sum w, w_c eps_c to sum w eps), assembles J^T W J and J^T W eps
+// and solves for the update delta = -b.  Singular when a diagonal entry is
+// <= 0 or a scaled pivot is <= pivot_tol; with fp64_pivot > 0 a system whose
+// smallest FP32 scaled pivot is below fp64_pivot is factorised again in FP64
+// and judged on the FP64 pivots.
+template <bool KAHAN>
+__device__ __forceinline__ bool solve_update(const Moments2& m, const Moments2& c, float wc, float ec,
+                                             float pivot_tol, float fp64_pivot, float delta[6]) {
+#define PC_FOLD(f) (KAHAN ? hsum(add2(m.f, c.f)) : hsum(m.f))
+    const float h00 = PC_FOLD(h00), h01 = -PC_FOLD(h01), h11 = PC_FOLD(h11);
+    const float s0 = PC_FOLD(s0), s1 = PC_FOLD(s1);
+    const float h03 = -PC_FOLD(h03), h04 = -PC_FOLD(h04), h05 = -PC_FOLD(h05);
+    const float h13 = PC_FOLD(h13), h14 = PC_FOLD(h14), h15 = PC_FOLD(h15);
+    const float sw = PC_FOLD(sw) + wc;
+    const float sxx = PC_FOLD(sxx), sxy = PC_FOLD(sxy), syy = PC_FOLD(syy);
+    const float m40 = PC_FOLD(m40), m31 = PC_FOLD(m31), m22 = PC_FOLD(m22), m13 = PC_FOLD(m13),
+                m04 = PC_FOLD(m04);
+    const float g0 = -PC_FOLD(g0), g1 = PC_FOLD(g1), ge = fmaf(wc, ec, PC_FOLD(ge));
+    const float g3 = PC_FOLD(g3), g4 = PC_FOLD(g4), g5 = PC_FOLD(g5);
+#undef PC_FOLD
     float H[6][6];
     H[0][0] = h00; H[0][1] = h01; H[0][2] = s0;
     H[0][3] = 0.5f * h03; H[0][4] = h04; H[0][5] = 0.5f * h05;
@@ -200,53 +298,23 @@ __device__ __forceinline__ bool solve_update(const Moments2& m, float wc, float 
     H[4][4] = m22; H[4][5] = 0.5f * m13;
     H[5][5] = 0.25f * m04;
     const float g[6] = {g0, g1, -ge, 0.5f * g3, g4, 0.5f * g5};
-    float D[6];
+    float mp;
+    bool pos;
+    ldlt6<float>(H, g, delta, mp, pos);
+    if (fp64_pivot > 0.f && pos && !(mp >= fp64_pivot)) {
+        double Hd[6][6], gd[6], dd[6], mpd;
 #pragma unroll
-    for (int i = 0; i < 6; i++) {
-        if (!(H[i][i] > 0.f)) return false;
-        D[i] = rsqrtf(H[i][i]);
-    }
-    float S[6][6], L[6][6], d[6];
+        for (int i = 0; i < 6; i++) {
+            gd[i] = g[i];
 #pragma unroll
-    for (int i = 0; i < 6; i++)
-#pragma unroll
-        for (int j = i; j < 6; j++) S[i][j] = H[i][j] * D[i] * D[j];
-#pragma unroll
-    for (int j = 0; j < 6; j++) {
-        float dj = S[j][j];
-#pragma unroll
-        for (int k = 0; k < j; k++) dj -= L[j][k] * L[j][k] * d[k];
-        if (!(dj > pivot_tol)) return false;
-        d[j] = dj;
-        const float idj = 1.f / dj;
-#pragma unroll
-        for (int i = j + 1; i < 6; i++) {
-            float s = S[j][i];
-#pragma unroll
-            for (int k = 0; k < j; k++) s -= L[i][k] * L[j][k] * d[k];
-            L[i][j] = s * idj;
+            for (int j = i; j < 6; j++) Hd[i][j] = H[i][j];
         }
+        ldlt6<double>(Hd, gd, dd, mpd, pos);
+#pragma unroll
+        for (int i = 0; i < 6; i++) delta[i] = (float)dd[i];
+        return pos && mpd > (double)pivot_tol;
     }
-    float z[6];
-#pragma unroll
-    for (int i = 0; i < 6; i++) {
-        float s = D[i] * g[i];
-#pragma unroll
-        for (int k = 0; k < i; k++) s -= L[i][k] * z[k];
-        z[i] = s;
-    }
-#pragma unroll
-    for (int i = 0; i < 6; i++) z[i] /= d[i];
-#pragma unroll
-    for (int i = 5; i >= 0; i--) {
-        float s = z[i];
-#pragma unroll
-        for (int k = i + 1; k < 6; k++) s -= L[k][i] * z[k];
-        z[i] = s;
-    }
-#pragma unroll
-    for (int i = 0; i < 6; i++) delta[i] = -D[i] * z[i];
-    return true;
+    return pos && mp > pivot_tol;
 }
 
 // R <- Rot(t0, t1, 0) R, Rot the rotation by angle |t| about t/|t|
@@ -330,9 +398,11 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
 // synchronise first).
 // RW > 0: window radius fixed at compile time, dense window, columns unrolled.
 // RW == 0: radius and stride from cfg.
-template <int RW, bool REJECT>
+template <int RW, bool REJECT, int PREC = 0>
 __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cfg, int tx_, int ty_,
                                          float* smem) {
+    constexpr bool KAHAN = (PREC & PREC_KAHAN) != 0;
+    constexpr int FMT = prec_format(PREC);
     const float* __restrict__ depth = f.depth;
     const int H = f.H, W = f.W;
     const Camera cam = f.cam;
@@ -357,7 +427,16 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
         const int gv = vb - halo + sy, gu = ub - halo + sx;
         float z = 0.f, c = __int_as_float(0x7f800000);
         if (gu >= 0 && gu < W && gv >= 0 && gv < H) {
-            const float d = __ldg(depth + (size_t)gv * W + gu);
+            float d;
+            if (FMT == 0) {
+                d = __ldg(depth + (size_t)gv * W + gu);
+            } else {
+                // centred 16-bit storage: range = tile base + offset
+                const unsigned short q = __ldg(f.packed + (size_t)gv * W + gu);
+                const float off = FMT == 1 ? __half2float(__ushort_as_half(q))
+                                           : __bfloat162float(__ushort_as_bfloat16(q));
+                d = __ldg(f.tile_base + (size_t)(gv / TILE_H) * ((W + TILE_W - 1) / TILE_W) + gu / TILE_W) + off;
+            }
             if (d > 0.f && d <= FLT_MAX) {
                 z = d;
                 c = 1.f;
@@ -474,15 +553,17 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
         }
         const float wcr = (REJECT && !(ec * ec <= thr)) ? 0.f : wc;
 
-        Moments2 m;
+        Moments2 m, comp;
         zero(m);
+        zero(comp);
         for_each_pair<RW>(zc, cc, SW, r, s, [&](float za, float zb, float ca, float cb, f32x2 DU,
                                                 f32x2 DV) {
-            visit2<REJECT>(m, k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1), mul2(DV, CY2), thr);
+            visit2<REJECT, KAHAN>(m, comp, k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1),
+                                  mul2(DV, CY2), thr);
         });
 
         float dl[6];
-        if (!solve_update(m, wcr, ec, cfg.pivot_tol, dl)) {
+        if (!solve_update<KAHAN>(m, comp, wcr, ec, cfg.pivot_tol, cfg.fp64_pivot, dl)) {
             ok = false;
             break;
         }
@@ -516,17 +597,21 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
     }
 }
 
-template <int RW, bool REJECT>
-__global__ void __launch_bounds__(BLOCK_THREADS, PC_MIN_BLOCKS) k_fit(FrameArgs f, FitConfig cfg) {
+// Compensated sums need a pair of registers more per sum: those variants keep
+// one CTA per SM instead of spilling.
+#define PC_BLOCKS_OF(PREC) (((PREC) & PREC_KAHAN) ? 1 : PC_MIN_BLOCKS)
+
+template <int RW, bool REJECT, int PREC = 0>
+__global__ void __launch_bounds__(BLOCK_THREADS, PC_BLOCKS_OF(PREC)) k_fit(FrameArgs f, FitConfig cfg) {
     extern __shared__ float smem[];
-    fit_tile<RW, REJECT>(f, cfg, blockIdx.x, blockIdx.y, smem);
+    fit_tile<RW, REJECT, PREC>(f, cfg, blockIdx.x, blockIdx.y, smem);
 }
 
 // Persistent form over many frames: the CTAs take (frame, tile) items from a
 // flattened queue with one atomic per tile until it is empty.  The header and
 // descriptors live in device memory (BatchTable); *next_tile must be 0 at launch.
-template <int RW, bool REJECT>
-__global__ void __launch_bounds__(BLOCK_THREADS, PC_MIN_BLOCKS)
+template <int RW, bool REJECT, int PREC = 0>
+__global__ void __launch_bounds__(BLOCK_THREADS, PC_BLOCKS_OF(PREC))
     k_fit_batch(const BatchTable* __restrict__ table, unsigned* __restrict__ next_tile, FitConfig cfg) {
     extern __shared__ float smem[];
     __shared__ int s_tile;
@@ -545,42 +630,42 @@ __global__ void __launch_bounds__(BLOCK_THREADS, PC_MIN_BLOCKS)
         }
         const int local = t - fr[lo].tile_begin, tiles_x = fr[lo].tiles_x;
         const int ty_ = local / tiles_x;
-        fit_tile<RW, REJECT>(fr[lo].f, cfg, local - ty_ * tiles_x, ty_, smem);
+        fit_tile<RW, REJECT, PREC>(fr[lo].f, cfg, local - ty_ * tiles_x, ty_, smem);
         __syncthreads();  // shared memory and s_tile are reused by the next tile
     }
 }
 
-template <int RW>
+template <int RW, int PREC = 0>
 cudaError_t launch_fit_rw(const FrameArgs& f, const FitConfig& cfg, cudaStream_t stream) {
     const dim3 block(TILE_W, TILE_H);
     const dim3 grid((f.W + TILE_W - 1) / TILE_W, (f.H + TILE_H - 1) / TILE_H);
     const size_t smem = fit_smem_bytes(cfg);
     if (cfg.reject)
-        k_fit<RW, true><<<grid, block, smem, stream>>>(f, cfg);
+        k_fit<RW, true, PREC><<<grid, block, smem, stream>>>(f, cfg);
     else
-        k_fit<RW, false><<<grid, block, smem, stream>>>(f, cfg);
+        k_fit<RW, false, PREC><<<grid, block, smem, stream>>>(f, cfg);
     return cudaGetLastError();
 }
 
-template <int RW>
+template <int RW, int PREC = 0>
 cudaError_t launch_batch_rw(const BatchTable* table, unsigned* next_tile, int grid, const FitConfig& cfg,
                             cudaStream_t stream) {
     const dim3 block(TILE_W, TILE_H);
     const size_t smem = fit_smem_bytes(cfg);
     if (cfg.reject)
-        k_fit_batch<RW, true><<<grid, block, smem, stream>>>(table, next_tile, cfg);
+        k_fit_batch<RW, true, PREC><<<grid, block, smem, stream>>>(table, next_tile, cfg);
     else
-        k_fit_batch<RW, false><<<grid, block, smem, stream>>>(table, next_tile, cfg);
+        k_fit_batch<RW, false, PREC><<<grid, block, smem, stream>>>(table, next_tile, cfg);
     return cudaGetLastError();
 }
 
-template <int RW>
+template <int RW, int PREC = 0>
 cudaError_t occupancy_rw(const FitConfig& cfg, int* blocks_per_sm) {
     const size_t smem = fit_smem_bytes(cfg);
     return cfg.reject
-               ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fit_batch<RW, true>,
+               ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fit_batch<RW, true, PREC>,
                                                                BLOCK_THREADS, smem)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fit_batch<RW, false>,
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fit_batch<RW, false, PREC>,
                                                                BLOCK_THREADS, smem);
 }
 

@@ -23,6 +23,8 @@ struct FitConfig {
     float det_tol;
     float pivot_tol;
     int min_window;
+    int kahan;         // compensated moment sums
+    float fp64_pivot;  // refactorise in FP64 below this scaled pivot (0 = never)
 };
 
 // Output tile of one CTA: TILE_W x TILE_H pixels, one thread per pixel.
@@ -47,6 +49,10 @@ struct FrameArgs {
     float* k1;
     float* k2;
     float* normal;  // may be nullptr
+    // centred 16-bit storage instead of depth (precision variants): per pixel
+    // an offset, per 32x8 tile an FP32 base
+    const unsigned short* packed;
+    const float* tile_base;
 };
 
 // A frame of a batch and its place in the flattened tile queue.
@@ -82,8 +88,17 @@ const KernelOps* ops_r5_8(int r);
 const KernelOps* ops_r9_12(int r);
 const KernelOps* ops_generic();
 
-// The instantiation serving cfg (dense radii 1..12 unrolled, anything else run-time).
+// Run-time-radius kernels of the precision variants: compensated sums and/or
+// 16-bit range storage (format 0 float32, 1 FP16, 2 BF16).
+const KernelOps* ops_precision(int kahan, int format);
+
+// The instantiation serving cfg (dense radii 1..12 unrolled, anything else
+// run-time; compensated sums on the precision kernels).
 const KernelOps* select_ops(const FitConfig& cfg);
+
+// Packs float32 ranges into per-tile-centred 16-bit storage (format 1 FP16, 2 BF16).
+cudaError_t launch_pack(const float* depth, int H, int W, int format, unsigned short* packed,
+                        float* tile_base, cudaStream_t stream);
 
 }  // namespace pcurv
 

@@ -113,7 +113,7 @@ extern "C" pc_status pc_compute_batch_static(pc_ctx* ctx, const pc_frame* frames
         pcurv::BatchFrame& d = t->frames[k++];
         d.f = pcurv::FrameArgs{f.depth, f.H, f.W,
                                pcurv::Camera{f.fx, f.fy, f.cx, f.cy, 1.f / f.fx, 1.f / f.fy},
-                               f.k1, f.k2, f.normal};
+                               f.k1, f.k2, f.normal, nullptr, nullptr};
         d.tiles_x = (f.W + pcurv::TILE_W - 1) / pcurv::TILE_W;
         d.tile_begin = begin;
         begin += d.tiles_x * ((f.H + pcurv::TILE_H - 1) / pcurv::TILE_H);

@@ -18,6 +18,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "pcurv.h")
 PC_OK, PC_ERR_INVALID_ARG, PC_ERR_CUDA, PC_ERR_OOM, PC_ERR_TIMEOUT, PC_ERR_UNSUPPORTED = range(6)
 PC_MAX_RADIUS, PC_MAX_NORMAL_RADIUS, PC_MAX_ITERATIONS, PC_MAX_DIM, PC_MAX_BATCH = 24, 8, 64, 16384, 4096
 PC_STATIC_MAX_FRAMES = 256
+PC_DEPTH_F16, PC_DEPTH_BF16 = 1, 2
+PC_PACK_TILE_W, PC_PACK_TILE_H = 32, 8
 
 
 class pc_params(ctypes.Structure):
@@ -31,6 +33,8 @@ class pc_params(ctypes.Structure):
         ("pivot_tol", ctypes.c_float),
         ("min_window", ctypes.c_int),
         ("batch_graph", ctypes.c_int),
+        ("kahan", ctypes.c_int),
+        ("fp64_solve_cond", ctypes.c_float),
     ]
 
 
@@ -70,13 +74,16 @@ def load() -> ctypes.CDLL:
         L.pc_compute_host.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.pc_compute_batch.argtypes = [_vp, ctypes.POINTER(pc_frame), ctypes.c_int, _vp]
         L.pc_compute_batch_static.argtypes = [_vp, ctypes.POINTER(pc_frame), ctypes.c_int, _vp]
+        L.pc_pack_depth.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+        L.pc_compute_packed.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
+                                        _vp, _vp, _vp]
         L.pc_destroy.argtypes = [_vp]
         L.pc_status_string.argtypes = [ctypes.c_int]
         L.pc_status_string.restype = ctypes.c_char_p
         L.pc_last_error.argtypes = [_vp]
         L.pc_last_error.restype = ctypes.c_char_p
         for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_compute_batch",
-                  "pc_compute_batch_static", "pc_destroy"):
+                  "pc_compute_batch_static", "pc_pack_depth", "pc_compute_packed", "pc_destroy"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -114,6 +121,14 @@ def pc_compute_batch(ctx, frames, n, stream) -> int:
 def pc_compute_batch_static(ctx, frames, n, stream) -> int:
     """The batch entry point that allocates no device memory (fixed scratch)."""
     return load().pc_compute_batch_static(ctx, frames, n, stream)
+
+
+def pc_pack_depth(ctx, depth, H, W, fmt, stream, packed, tile_base) -> int:
+    return load().pc_pack_depth(ctx, depth, H, W, fmt, stream, packed, tile_base)
+
+
+def pc_compute_packed(ctx, packed, tile_base, fmt, H, W, stream, k1_out, k2_out, normal_out) -> int:
+    return load().pc_compute_packed(ctx, packed, tile_base, fmt, H, W, stream, k1_out, k2_out, normal_out)
 
 
 def pc_destroy(ctx) -> int:
@@ -202,6 +217,31 @@ class Curvature:
         st = pc_compute_batch(self.ctx, arr if frames else None, len(frames), _stream_handle(stream))
         if st != PC_OK:
             raise PcError(st, "pc_compute_batch", pc_last_error(self.ctx))
+
+    def pack(self, depth, fmt, stream=None):
+        """pc_pack_depth: returns (packed int16 tensor H x W, tile_base float tensor)."""
+        import torch
+        H, W = depth.shape
+        packed = torch.empty((H, W), dtype=torch.int16, device=depth.device)
+        base = torch.empty(((H + 7) // 8, (W + 31) // 32), dtype=torch.float32, device=depth.device)
+        st = pc_pack_depth(self.ctx, depth.contiguous().data_ptr(), H, W, fmt, _stream_handle(stream),
+                           packed.data_ptr(), base.data_ptr())
+        if st != PC_OK:
+            raise PcError(st, "pc_pack_depth", pc_last_error(self.ctx))
+        return packed, base
+
+    def compute_packed(self, packed, base, fmt, stream=None, want_normal=True):
+        """pc_compute_packed on the storage made by pack(); returns (k1, k2, normal)."""
+        import torch
+        H, W = packed.shape
+        k1 = torch.empty((H, W), device=packed.device)
+        k2 = torch.empty((H, W), device=packed.device)
+        normal = torch.empty((H, W, 3), device=packed.device) if want_normal else None
+        st = pc_compute_packed(self.ctx, packed.data_ptr(), base.data_ptr(), fmt, H, W, _stream_handle(stream),
+                               k1.data_ptr(), k2.data_ptr(), normal.data_ptr() if normal is not None else None)
+        if st != PC_OK:
+            raise PcError(st, "pc_compute_packed", pc_last_error(self.ctx))
+        return k1, k2, normal
 
     def compute_host(self, depth, k1, k2, normal=None, stream=None):
         """Host-memory form (pc_compute_host): depth, k1, k2, normal are CPU

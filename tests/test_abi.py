@@ -43,6 +43,7 @@ def test_params_struct_matches_header(pc):
     body = re.search(r"typedef struct pc_params \{(.*?)\} pc_params;", text, re.S).group(1)
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"(float|int)\s+(\w+);", body)
+    assert len(fields) == len(pc.pc_params._fields_)
     assert [f for _, f in fields] == [f for f, _ in pc.pc_params._fields_]
     ctype = {"float": ctypes.c_float, "int": ctypes.c_int}
     assert all(ctype[t] is c for (t, _), (_, c) in zip(fields, pc.pc_params._fields_))
@@ -88,7 +89,7 @@ def test_batch_argument_checks_without_gpu(pc):
 def test_limits_match_header(pc):
     text = open(HEADER).read()
     for name in ("PC_MAX_RADIUS", "PC_MAX_NORMAL_RADIUS", "PC_MAX_ITERATIONS", "PC_MAX_DIM", "PC_MAX_BATCH",
-                 "PC_STATIC_MAX_FRAMES"):
+                 "PC_STATIC_MAX_FRAMES", "PC_DEPTH_F16", "PC_DEPTH_BF16", "PC_PACK_TILE_W", "PC_PACK_TILE_H"):
         val = int(re.search(rf"#define {name} (\d+)", text).group(1))
         assert getattr(pc.pcurv, name) == val
 
@@ -98,7 +99,7 @@ def test_defaults(pc):
     assert p.k == pytest.approx(1e-4) and p.reject == 0 and p.reject_ratio == 2.0
     assert p.normal_radius == 3 and p.stride == 1 and p.min_window == 6
     assert p.pivot_tol == pytest.approx(1e-5) and p.det_tol == pytest.approx(1e-6)
-    assert p.batch_graph == 1
+    assert p.batch_graph == 1 and p.kahan == 0 and p.fp64_solve_cond == 0.0
 
 
 def test_status_strings(pc):
@@ -122,7 +123,7 @@ def test_create_rejects_bad_arguments(pc, args):
                                          ("reject_ratio", 0.0), ("normal_radius", 0),
                                          ("normal_radius", 9), ("stride", 0), ("min_window", 5),
                                          ("pivot_tol", -1.0), ("det_tol", float("inf")),
-                                         ("batch_graph", 2)])
+                                         ("batch_graph", 2), ("kahan", 3), ("fp64_solve_cond", -1.0)])
 def test_create_rejects_bad_params(pc, field, value):
     p = pc.pc_params_default()
     setattr(p, field, value)
@@ -151,6 +152,19 @@ def test_compute_argument_checks_without_gpu(pc):
         assert pc.pc_destroy(ctx) == pc.PC_OK
     assert pc.pc_destroy(None) == pc.PC_OK
     assert pc.pc_last_error(None) == ""
+
+
+def test_pack_argument_checks_without_gpu(pc):
+    st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5)
+    try:
+        assert pc.pc_pack_depth(ctx, None, 4, 4, 3, None, None, None) == pc.PC_ERR_INVALID_ARG   # format
+        assert pc.pc_pack_depth(ctx, None, 0, 4, 1, None, None, None) == pc.PC_OK
+        assert pc.pc_pack_depth(ctx, None, 4, 4, 1, None, None, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute_packed(ctx, None, None, 0, 4, 4, None, None, None, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute_packed(ctx, None, None, 2, 4, 4, None, None, None, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute_packed(ctx, None, None, 2, 4, 0, None, None, None, None) == pc.PC_OK
+    finally:
+        pc.pc_destroy(ctx)
 
 
 def test_binding_fails_loudly_without_library(pc, monkeypatch, tmp_path):
