@@ -63,7 +63,9 @@ def parse():
     ap.add_argument("--scenes", type=int, default=SCENES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--report", choices=["precision"], default=None,
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--report", choices=["precision", "serve"], default=None,
                     help="instead of the benchmark line, print the error of each precision variant "
                          "against the FP64 oracle (one 640x480 frame, radii 3, 7, 11)")
     return ap.parse_args()
@@ -229,6 +231,35 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def serve_trace(scenes_, n, rate, seed, batched=True, plain=True):
+    """Serves n requests arriving as a Poisson process at `rate` per second,
+    each a frame drawn uniformly from scenes_ (host, page-locked), with the
+    continuous-batching server and with one launch per frame."""
+    import torch
+    from paper_1707_00385_gb300.serve import (GpuExecutor, PlainExecutor, Request, Server, device_budget,
+                                              poisson_arrivals)
+    pool = [(torch.from_numpy(s.depth).pin_memory(), s.intrinsics) for s in scenes_]
+    rng = np.random.default_rng(seed)
+    t = poisson_arrivals(n, rate, seed)
+    pick = rng.integers(0, len(pool), n)
+    budget = device_budget(0.5)
+    out = {"requests": n, "offered_per_s": rate, "resolutions": [f"{w}x{h}" for h, w, _ in UNEVEN_SIZES],
+           "budget_bytes": budget}
+    modes = ([("continuous_batching", GpuExecutor, dict(max_batch_frames=64, inflight=2))] if batched else []) + \
+            ([("one_launch_per_frame", PlainExecutor, dict(max_batch_frames=1, inflight=64))] if plain else [])
+    for name, Ex, kw in modes:
+        ex = Ex(RADIUS, ITERS)
+        warm = [Request(-1 - i, *pool[i % len(pool)], 0.0) for i in range(len(pool))]
+        Server(ex, budget, **kw).run(warm)
+        reqs = [Request(i, *pool[pick[i]], float(t[i])) for i in range(n)]
+        st = Server(ex, budget, **kw).run(reqs)
+        ex.close()
+        out[name] = {"frames_per_s": st.frames_per_s, "mpixel_per_s": st.mpixel_per_s, "p50_ms": st.p50_ms,
+                     "p99_ms": st.p99_ms, "mean_batch": st.mean_batch, "batches": st.batches,
+                     "peak_device_bytes": st.peak_device_bytes}
+    return out
+
+
 def precision_report(args):
     """Error of each precision variant against the FP64 oracle on one seeded
     640x480 Kinect-like frame, per window radius, with its time per frame."""
@@ -285,6 +316,16 @@ def main():
     args = parse()
     if args.report == "precision":
         precision_report(args)
+        return
+    if args.report == "serve":
+        # SURVEY config 5: 20,000 requests at 2,000/s, then a point at half the
+        # measured batched capacity
+        un = uneven_scenes(2)
+        full = serve_trace(un, args.serve_requests, args.serve_rate, seed=11)
+        print(json.dumps({"serve": full}), flush=True)
+        cap = full["continuous_batching"]["frames_per_s"]
+        half = serve_trace(un, args.serve_requests, 0.5 * cap, seed=12)
+        print(json.dumps({"serve_half_capacity": half}), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -399,6 +440,10 @@ def main():
     for c_ in un_ctx:
         c_.close()
 
+    # ---- serving: Poisson arrivals of the mixed-resolution frames, continuous
+    # batching vs one launch per frame (same frames, same trace)
+    serve_res = serve_trace(un, args.serve_requests, args.serve_rate, seed=11)
+
     # ---- end to end through the host-memory entry point (pinned buffers)
     hd = [torch.from_numpy(h).pin_memory() for h in host]
     hk1 = [torch.empty((H, W)).pin_memory() for _ in range(F)]
@@ -454,6 +499,7 @@ def main():
                     "matches_device_path": same},
             "per_frame_launches": {"value": pf_value, "unit": "Mpixel/s", "ms_per_frame": ms_pf / max(2, args.steps // 2) / F},
             "uneven_batch": uneven,
+            "serve": serve_res,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "roofline": roof}
