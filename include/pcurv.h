@@ -91,6 +91,10 @@ typedef struct pc_params {
                             (1 / smallest scaled pivot) exceeds this value, the 6x6 system is
                             factorised again in FP64 and singularity is judged on the FP64
                             pivots. 0 = off (default) */
+    int tile_height;     /* pixel rows of the 32-column tile one CTA computes: 8 or 4; 0 = choose
+                            per image (the size's pc_autotune result when there is one, else 8
+                            when the image has at least 1.5 32x8 tiles per SM, else 4).  Results
+                            do not depend on it.  Default 0 */
 } pc_params;
 
 /* Writes the defaults above into *p (no-op for NULL). */
@@ -190,6 +194,18 @@ pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* str
  *     synchronise in between. */
 #define PC_STATIC_MAX_FRAMES 256
 pc_status pc_compute_batch_static(pc_ctx* ctx, const pc_frame* frames, int n, void* stream);
+
+/* Times the tile shapes on this image (one warm-up and three timed runs of
+ * each, on `stream`, which it synchronises), remembers the fastest for images
+ * of this H x W in ctx (up to 16 sizes; the oldest is forgotten first) and
+ * leaves the last run's results in the outputs (layouts as pc_compute).
+ * Has no effect on the choice when params.tile_height is not 0. */
+pc_status pc_autotune(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* k1_out,
+                      float* k2_out, float* normal_out);
+
+/* Tile height (8 or 4) pc_compute uses for an H x W image on the current
+ * device; 0 for a NULL context or sizes out of range. */
+int pc_plan_tile_height(pc_ctx* ctx, int H, int W);
 
 /* Frees the context, its staging buffers, batch scratch and graphs
  * (synchronising the device first when it owns any).  NULL is a no-op

@@ -26,9 +26,16 @@ struct BatchScratch {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_grid[2] = {0, 0};
     int graph_cap[2] = {0, 0};
+    int graph_variant[2] = {-1, -1};
     cudaStream_t capture = nullptr;           // private stream used only for capture
-    int grid = 0;                             // persistent CTAs
+    int grid[pcurv::NUM_TILE_VARIANTS] = {0, 0};  // persistent CTAs per tile variant
     int next = 0;                             // staging copy of the next call
+};
+
+// Tile variant chosen by pc_autotune for one image size.
+struct Plan {
+    int H = 0, W = 0, variant = 0;
+    long long stamp = 0;
 };
 
 }  // namespace
@@ -45,6 +52,10 @@ struct pc_ctx {
     float* d_k2 = nullptr;
     float* d_normal = nullptr;
     BatchScratch batch;
+    Plan plans[16];
+    long long plan_clock = 0;
+    int sms_device = -1;
+    int sms = 0;                              // SMs of that device
     char last_error[256] = {0};
 };
 
@@ -80,6 +91,7 @@ pc_status check_params(const pc_params& p) {
     if (p.min_window < 6) return PC_ERR_INVALID_ARG;  // six parameters need six points
     if (p.batch_graph != 0 && p.batch_graph != 1) return PC_ERR_INVALID_ARG;
     if (p.kahan != 0 && p.kahan != 1) return PC_ERR_INVALID_ARG;
+    if (p.tile_height != 0 && p.tile_height != 8 && p.tile_height != 4) return PC_ERR_INVALID_ARG;
     if (!(finite_f(p.fp64_solve_cond) && p.fp64_solve_cond >= 0.f)) return PC_ERR_INVALID_ARG;
     return PC_OK;
 }
@@ -110,6 +122,7 @@ void release_batch(BatchScratch& b) {
         if (b.graph[i]) cudaGraphExecDestroy(b.graph[i]);
         b.graph[i] = nullptr;
         b.graph_grid[i] = b.graph_cap[i] = 0;
+        b.graph_variant[i] = -1;
         if (b.h_table[i]) cudaFreeHost(b.h_table[i]);
         b.h_table[i] = nullptr;
         if (b.done[i]) cudaEventDestroy(b.done[i]);
@@ -122,7 +135,7 @@ void release_batch(BatchScratch& b) {
     if (b.capture) cudaStreamDestroy(b.capture);
     b.capture = nullptr;
     b.cap = 0;
-    b.grid = 0;
+    b.grid[0] = b.grid[1] = 0;
     b.device = -1;
 }
 
@@ -155,6 +168,62 @@ void ctx_set_error(pc_ctx* ctx, const char* msg) {
 
 }  // namespace pcurv
 
+namespace {
+
+// SMs of the current device (cached per device in ctx).
+cudaError_t sm_count(pc_ctx* ctx, int* sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (ctx->sms_device != dev) {
+        if ((e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
+        ctx->sms_device = dev;
+    }
+    *sms = ctx->sms;
+    return cudaSuccess;
+}
+
+int forced_variant(const pc_ctx* ctx) {
+    return ctx->params.tile_height == 8 ? 0 : ctx->params.tile_height == 4 ? 1 : -1;
+}
+
+// 32 x 8 tiles when there are at least 1.5 per SM, else 32 x 4 (GB300:
+// 32 x 4 is a third faster at 160 x 120, even at 320 x 240).
+int heuristic_variant(long long tiles8, int sms) { return 2 * tiles8 >= 3LL * sms ? 0 : 1; }
+
+// Tile variant for one H x W image: forced, tuned, or the heuristic; always
+// one that ops has.
+cudaError_t variant_for(pc_ctx* ctx, const pcurv::KernelOps* ops, int H, int W, int* v) {
+    int choice = forced_variant(ctx);
+    if (choice < 0) {
+        for (const Plan& pl : ctx->plans)
+            if (pl.stamp && pl.H == H && pl.W == W) choice = pl.variant;
+    }
+    if (choice < 0) {
+        int sms = 0;
+        const cudaError_t e = sm_count(ctx, &sms);
+        if (e != cudaSuccess) return e;
+        choice = heuristic_variant(pcurv::tiles_of(H, W, 8), sms);
+    }
+    *v = ops->fit[choice] ? choice : 0;
+    return cudaSuccess;
+}
+
+void remember_plan(pc_ctx* ctx, int H, int W, int variant) {
+    Plan* slot = &ctx->plans[0];
+    for (Plan& pl : ctx->plans) {
+        if (pl.stamp && pl.H == H && pl.W == W) { slot = &pl; break; }
+        if (pl.stamp < slot->stamp) slot = &pl;
+    }
+    slot->H = H;
+    slot->W = W;
+    slot->variant = variant;
+    slot->stamp = ++ctx->plan_clock;
+}
+
+}  // namespace
+
 extern "C" {
 
 void pc_params_default(pc_params* p) {
@@ -170,6 +239,7 @@ void pc_params_default(pc_params* p) {
     p->batch_graph = 1;
     p->kahan = 0;
     p->fp64_solve_cond = 0.f;
+    p->tile_height = 0;
 }
 
 pc_status pc_create(float fx, float fy, float cx, float cy, int window_radius, int iterations,
@@ -203,9 +273,62 @@ pc_status pc_compute(pc_ctx* ctx, const float* depth, int H, int W, void* stream
     if (H == 0 || W == 0) return PC_OK;
     if ((st = check_buffers(depth, k1_out, k2_out, normal_out)) != PC_OK) return st;
     const pcurv::FrameArgs f{depth, H, W, ctx->cam, k1_out, k2_out, normal_out, nullptr, nullptr};
-    const cudaError_t e = pcurv::select_ops(ctx->cfg)->fit(f, ctx->cfg, (cudaStream_t)stream);
+    const pcurv::KernelOps* ops = pcurv::select_ops(ctx->cfg);
+    int v = 0;
+    cudaError_t e = variant_for(ctx, ops, H, W, &v);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute plan");
+    e = ops->fit[v](f, ctx->cfg, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute launch");
     return PC_OK;
+}
+
+pc_status pc_autotune(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* k1_out,
+                      float* k2_out, float* normal_out) {
+    if (!ctx) return PC_ERR_INVALID_ARG;
+    pc_status st = check_image(H, W);
+    if (st != PC_OK) return st;
+    if (H == 0 || W == 0) return PC_OK;
+    if ((st = check_buffers(depth, k1_out, k2_out, normal_out)) != PC_OK) return st;
+    const pcurv::FrameArgs f{depth, H, W, ctx->cam, k1_out, k2_out, normal_out, nullptr, nullptr};
+    const pcurv::KernelOps* ops = pcurv::select_ops(ctx->cfg);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(ctx, e, "pc_autotune events");
+    }
+    int best = 0;
+    float best_ms = 3.4e38f;
+    for (int v = 0; v < pcurv::NUM_TILE_VARIANTS && e == cudaSuccess; v++) {
+        if (!ops->fit[v]) continue;
+        e = ops->fit[v](f, ctx->cfg, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int i = 0; i < 3 && e == cudaSuccess; i++) e = ops->fit[v](f, ctx->cfg, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_autotune");
+    remember_plan(ctx, H, W, best);
+    return PC_OK;
+}
+
+int pc_plan_tile_height(pc_ctx* ctx, int H, int W) {
+    if (!ctx || check_image(H, W) != PC_OK) return 0;
+    int v = 0;
+    if (variant_for(ctx, pcurv::select_ops(ctx->cfg), H, W, &v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return pcurv::tile_h_of(v);
 }
 
 static bool aligned2(const void* p) { return ((uintptr_t)p & 1u) == 0; }
@@ -239,7 +362,7 @@ pc_status pc_compute_packed(pc_ctx* ctx, const unsigned short* packed, const flo
         return PC_ERR_INVALID_ARG;
     const pcurv::FrameArgs f{nullptr, H, W, ctx->cam, k1_out, k2_out, normal_out, packed, tile_base};
     const cudaError_t e =
-        pcurv::ops_precision(ctx->cfg.kahan, format)->fit(f, ctx->cfg, (cudaStream_t)stream);
+        pcurv::ops_precision(ctx->cfg.kahan, format)->fit[0](f, ctx->cfg, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_packed launch");
     return PC_OK;
 }
@@ -287,7 +410,10 @@ pc_status pc_compute_host(pc_ctx* ctx, const float* depth_host, int H, int W, vo
         return cuda_fail(ctx, e, "depth H2D");
     const pcurv::FrameArgs f{ctx->d_depth, H, W, ctx->cam, ctx->d_k1, ctx->d_k2,
                              normal_host ? ctx->d_normal : nullptr, nullptr, nullptr};
-    e = pcurv::select_ops(ctx->cfg)->fit(f, ctx->cfg, s);
+    const pcurv::KernelOps* ops = pcurv::select_ops(ctx->cfg);
+    int v = 0;
+    if ((e = variant_for(ctx, ops, H, W, &v)) != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_host plan");
+    e = ops->fit[v](f, ctx->cfg, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_host launch");
     if ((e = cudaMemcpyAsync(k1_host, ctx->d_k1, npx * sizeof(float), cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess ||
@@ -312,10 +438,12 @@ static pc_status ensure_batch(pc_ctx* ctx, int n) {
     const int cap = round_up_pow2(n < 16 ? 16 : n);
     const size_t bytes = pcurv::batch_table_bytes(cap);
     const pcurv::KernelOps* ops = pcurv::select_ops(ctx->cfg);
-    int sms = 0, bps = 0;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-        (e = ops->occupancy(ctx->cfg, &bps)) != cudaSuccess)
+    int sms = 0, bps[pcurv::NUM_TILE_VARIANTS] = {0, 0};
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return cuda_fail(ctx, e, "batch occupancy");
+    for (int v = 0; v < pcurv::NUM_TILE_VARIANTS; v++)
+        if (ops->occupancy[v] && (e = ops->occupancy[v](ctx->cfg, &bps[v])) != cudaSuccess)
+            return cuda_fail(ctx, e, "batch occupancy");
     if ((e = cudaMalloc(&b.d_table, bytes)) != cudaSuccess ||
         (e = cudaMalloc(&b.d_counter, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaHostAlloc(&b.h_table[0], bytes, cudaHostAllocDefault)) != cudaSuccess ||
@@ -328,29 +456,32 @@ static pc_status ensure_batch(pc_ctx* ctx, int n) {
     }
     b.device = dev;
     b.cap = cap;
-    b.grid = sms * (bps > 0 ? bps : 1);
+    for (int v = 0; v < pcurv::NUM_TILE_VARIANTS; v++) b.grid[v] = sms * (bps[v] > 0 ? bps[v] : 1);
     return PC_OK;
 }
 
-// Copy of the staged table, queue reset and persistent kernel, on `s`.
-static cudaError_t enqueue_batch(pc_ctx* ctx, int slot, size_t bytes, cudaStream_t s) {
+// Copy of the staged table, queue reset and persistent kernel (tile variant v), on `s`.
+static cudaError_t enqueue_batch(pc_ctx* ctx, int slot, size_t bytes, int v, cudaStream_t s) {
     BatchScratch& b = ctx->batch;
     cudaError_t e = cudaMemcpyAsync(b.d_table, b.h_table[slot], bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-    return pcurv::select_ops(ctx->cfg)->batch(b.d_table, b.d_counter, b.grid, ctx->cfg, s);
+    return pcurv::select_ops(ctx->cfg)->batch[v](b.d_table, b.d_counter, b.grid[v], ctx->cfg, s);
 }
 
-// The graph of staging copy `slot` (captured on the private stream once per capacity).
-static pc_status ensure_graph(pc_ctx* ctx, int slot) {
+// The graph of staging copy `slot` (captured on the private stream once per
+// capacity and tile variant).
+static pc_status ensure_graph(pc_ctx* ctx, int slot, int v) {
     BatchScratch& b = ctx->batch;
-    if (b.graph[slot] && b.graph_cap[slot] == b.cap && b.graph_grid[slot] == b.grid) return PC_OK;
+    if (b.graph[slot] && b.graph_cap[slot] == b.cap && b.graph_grid[slot] == b.grid[v] &&
+        b.graph_variant[slot] == v)
+        return PC_OK;
     if (b.graph[slot]) cudaGraphExecDestroy(b.graph[slot]);
     b.graph[slot] = nullptr;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b.capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture begin");
-    const cudaError_t e1 = enqueue_batch(ctx, slot, pcurv::batch_table_bytes(b.cap), b.capture);
+    const cudaError_t e1 = enqueue_batch(ctx, slot, pcurv::batch_table_bytes(b.cap), v, b.capture);
     e = cudaStreamEndCapture(b.capture, &g);
     if (e1 != cudaSuccess || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -363,13 +494,14 @@ static pc_status ensure_graph(pc_ctx* ctx, int slot) {
         return cuda_fail(ctx, e, "graph instantiate");
     }
     b.graph_cap[slot] = b.cap;
-    b.graph_grid[slot] = b.grid;
+    b.graph_grid[slot] = b.grid[v];
+    b.graph_variant[slot] = v;
     return PC_OK;
 }
 
 pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream) {
     if (!ctx || n < 0 || n > PC_MAX_BATCH || (n > 0 && !frames)) return PC_ERR_INVALID_ARG;
-    long long total = 0;
+    long long total = 0;  // 32 x 8 tiles
     int live = 0;
     for (int i = 0; i < n; i++) {
         const pc_frame& fr = frames[i];
@@ -378,15 +510,24 @@ pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* str
         if (fr.H == 0 || fr.W == 0) continue;
         if (!valid_intrinsics(fr.fx, fr.fy, fr.cx, fr.cy)) return PC_ERR_INVALID_ARG;
         if ((st = check_buffers(fr.depth, fr.k1, fr.k2, fr.normal)) != PC_OK) return st;
-        total += (long long)((fr.W + pcurv::TILE_W - 1) / pcurv::TILE_W) *
-                 ((fr.H + pcurv::TILE_H - 1) / pcurv::TILE_H);
+        total += pcurv::tiles_of(fr.H, fr.W, 8);
         live++;
     }
     if (live == 0) return PC_OK;
-    if (total > 0x7fffffffLL) return PC_ERR_INVALID_ARG;
+    if (2 * total > 0x7fffffffLL) return PC_ERR_INVALID_ARG;
     pc_status st = ensure_batch(ctx, live);
     if (st != PC_OK) return st;
     BatchScratch& b = ctx->batch;
+    const pcurv::KernelOps* ops = pcurv::select_ops(ctx->cfg);
+    int v = forced_variant(ctx);
+    if (v < 0) {
+        int sms = 0;
+        cudaError_t es = sm_count(ctx, &sms);
+        if (es != cudaSuccess) return cuda_fail(ctx, es, "batch plan");
+        v = heuristic_variant(total, sms);
+    }
+    if (!ops->batch[v]) v = 0;
+    const int th = pcurv::tile_h_of(v);
     const int slot = b.next;
     b.next ^= 1;
     cudaError_t e;
@@ -406,15 +547,15 @@ pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* str
                                fr.k1, fr.k2, fr.normal, nullptr, nullptr};
         d.tiles_x = (fr.W + pcurv::TILE_W - 1) / pcurv::TILE_W;
         d.tile_begin = begin;
-        begin += d.tiles_x * ((fr.H + pcurv::TILE_H - 1) / pcurv::TILE_H);
+        begin += d.tiles_x * ((fr.H + th - 1) / th);
     }
     t->nframes = live;
     t->total_tiles = begin;
     cudaStream_t s = (cudaStream_t)stream;
     if (ctx->params.batch_graph) {
-        if ((st = ensure_graph(ctx, slot)) != PC_OK) return st;
+        if ((st = ensure_graph(ctx, slot, v)) != PC_OK) return st;
         if ((e = cudaGraphLaunch(b.graph[slot], s)) != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
-    } else if ((e = enqueue_batch(ctx, slot, pcurv::batch_table_bytes(live), s)) != cudaSuccess) {
+    } else if ((e = enqueue_batch(ctx, slot, pcurv::batch_table_bytes(live), v, s)) != cudaSuccess) {
         return cuda_fail(ctx, e, "batch launch");
     }
     if ((e = cudaEventRecord(b.done[slot], s)) != cudaSuccess) return cuda_fail(ctx, e, "batch event");

@@ -1,6 +1,7 @@
 // pc_fit.cuh -- the fused per-pixel curvature kernel (sm_103a).
 //
-// One CTA computes a 32 x 8 tile of output pixels, one thread per pixel.  The
+// One CTA computes a 32 x th tile of output pixels (th = 8 or 4), one thread
+// per pixel.  The
 // CTA first stages the tile's range values plus a halo of max(r, r_n) pixels
 // into shared memory as two planes, Z and c, c = 1 for a valid range and +inf
 // for none (outside the image, zero, negative or not finite), and counts the
@@ -211,6 +212,17 @@ __device__ __forceinline__ float sq_residual2(const Coef2& k, float za, float zb
     return (ca == 1.f ? ea : 0.f) + (cb == 1.f ? eb : 0.f);
 }
 
+// 1/sqrt(x) and 1/x: hardware approximations in single precision (at most
+// 2 and 1 ulp: PTX rsqrt.approx, rcp.approx), correctly rounded in double.
+__device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float inv(float x) {
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ double inv(double x) { return 1.0 / x; }
+
 // Jacobi-scaled LDL^T solve of H b = g (H symmetric, upper triangle used),
 // returning delta = -b and the smallest scaled pivot.  T is float or double.
 template <typename T>
@@ -221,7 +233,7 @@ __device__ __forceinline__ void ldlt6(const T (&H)[6][6], const T (&g)[6], T del
 #pragma unroll
     for (int i = 0; i < 6; i++) {
         positive_diag = positive_diag && (H[i][i] > T(0));
-        D[i] = T(1) / sqrt(H[i][i] > T(0) ? H[i][i] : T(1));
+        D[i] = inv_sqrt(H[i][i] > T(0) ? H[i][i] : T(1));
     }
     T S[6][6], L[6][6], d[6];
 #pragma unroll
@@ -237,7 +249,7 @@ __device__ __forceinline__ void ldlt6(const T (&H)[6][6], const T (&g)[6], T del
         min_pivot = dj < min_pivot ? dj : min_pivot;
         min_pivot = dj == dj ? min_pivot : T(-1);  // NaN counts as singular
         d[j] = dj;
-        const T idj = T(1) / dj;
+        const T idj = inv(dj);
 #pragma unroll
         for (int i = j + 1; i < 6; i++) {
             T s = S[j][i];
@@ -246,7 +258,9 @@ __device__ __forceinline__ void ldlt6(const T (&H)[6][6], const T (&g)[6], T del
             L[i][j] = s * idj;
         }
     }
-    T z[6];
+    T z[6], id[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) id[i] = inv(d[i]);
 #pragma unroll
     for (int i = 0; i < 6; i++) {
         T s = D[i] * g[i];
@@ -255,7 +269,7 @@ __device__ __forceinline__ void ldlt6(const T (&H)[6][6], const T (&g)[6], T del
         z[i] = s;
     }
 #pragma unroll
-    for (int i = 0; i < 6; i++) z[i] /= d[i];
+    for (int i = 0; i < 6; i++) z[i] *= id[i];
 #pragma unroll
     for (int i = 5; i >= 0; i--) {
         T s = z[i];
@@ -392,15 +406,16 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
     }
 }
 
-// The whole method for one 32 x 8 output tile (tile column tx_, tile row ty_)
+// The whole method for one 32 x TH output tile (tile column tx_, tile row ty_)
 // of frame f.  Called by every thread of the CTA; contains two __syncthreads
 // and leaves shared memory in use until it returns (callers that reuse smem
 // synchronise first).
 // RW > 0: window radius fixed at compile time, dense window, columns unrolled.
 // RW == 0: radius and stride from cfg.
-template <int RW, bool REJECT, int PREC = 0>
+template <int RW, bool REJECT, int PREC = 0, int TH = 8>
 __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cfg, int tx_, int ty_,
                                          float* smem) {
+    constexpr int NT = TILE_W * TH;  // threads
     constexpr bool KAHAN = (PREC & PREC_KAHAN) != 0;
     constexpr int FMT = prec_format(PREC);
     const float* __restrict__ depth = f.depth;
@@ -414,15 +429,15 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
     const int r0 = (r / s) * s;   // largest sampled offset
     const int halo = r > cfg.rn ? r : cfg.rn;
     const int SW = TILE_W + 2 * halo;
-    const int SH = TILE_H + 2 * halo;
+    const int SH = TH + 2 * halo;
     float* tz = smem;                       // Z plane, SH x SW
     float* tcv = smem + SW * SH;            // c plane
     int* rcnt = (int*)(tcv + SW * SH);      // valid window points per (tile row, pixel column)
-    const int ub = tx_ * TILE_W, vb = ty_ * TILE_H;
+    const int ub = tx_ * TILE_W, vb = ty_ * TH;
     const int tid = threadIdx.y * TILE_W + threadIdx.x;
 
     // stage the tile + halo (Sec. 3.2, first item: the range image)
-    for (int i = tid; i < SW * SH; i += BLOCK_THREADS) {
+    for (int i = tid; i < SW * SH; i += NT) {
         const int sy = i / SW, sx = i - sy * SW;
         const int gv = vb - halo + sy, gu = ub - halo + sx;
         float z = 0.f, c = __int_as_float(0x7f800000);
@@ -435,7 +450,8 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
                 const unsigned short q = __ldg(f.packed + (size_t)gv * W + gu);
                 const float off = FMT == 1 ? __half2float(__ushort_as_half(q))
                                            : __bfloat162float(__ushort_as_bfloat16(q));
-                d = __ldg(f.tile_base + (size_t)(gv / TILE_H) * ((W + TILE_W - 1) / TILE_W) + gu / TILE_W) + off;
+                d = __ldg(f.tile_base + (size_t)(gv / PACK_TILE_H) * ((W + TILE_W - 1) / TILE_W) + gu / TILE_W) +
+                    off;
             }
             if (d > 0.f && d <= FLT_MAX) {
                 z = d;
@@ -447,7 +463,7 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
     }
     __syncthreads();
     // valid points of each window row segment (columns -r0..r0 on the stride)
-    for (int i = tid; i < SH * TILE_W; i += BLOCK_THREADS) {
+    for (int i = tid; i < SH * TILE_W; i += NT) {
         const int row = i / TILE_W, col = i - row * TILE_W;
         const float* c = tcv + row * SW + col + halo;
         int n = 0;
@@ -601,17 +617,17 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
 // one CTA per SM instead of spilling.
 #define PC_BLOCKS_OF(PREC) (((PREC) & PREC_KAHAN) ? 1 : PC_MIN_BLOCKS)
 
-template <int RW, bool REJECT, int PREC = 0>
-__global__ void __launch_bounds__(BLOCK_THREADS, PC_BLOCKS_OF(PREC)) k_fit(FrameArgs f, FitConfig cfg) {
+template <int RW, bool REJECT, int PREC, int TH>
+__global__ void __launch_bounds__(TILE_W * TH, PC_BLOCKS_OF(PREC) * (8 / TH)) k_fit(FrameArgs f, FitConfig cfg) {
     extern __shared__ float smem[];
-    fit_tile<RW, REJECT, PREC>(f, cfg, blockIdx.x, blockIdx.y, smem);
+    fit_tile<RW, REJECT, PREC, TH>(f, cfg, blockIdx.x, blockIdx.y, smem);
 }
 
 // Persistent form over many frames: the CTAs take (frame, tile) items from a
 // flattened queue with one atomic per tile until it is empty.  The header and
 // descriptors live in device memory (BatchTable); *next_tile must be 0 at launch.
-template <int RW, bool REJECT, int PREC = 0>
-__global__ void __launch_bounds__(BLOCK_THREADS, PC_BLOCKS_OF(PREC))
+template <int RW, bool REJECT, int PREC, int TH>
+__global__ void __launch_bounds__(TILE_W * TH, PC_BLOCKS_OF(PREC) * (8 / TH))
     k_fit_batch(const BatchTable* __restrict__ table, unsigned* __restrict__ next_tile, FitConfig cfg) {
     extern __shared__ float smem[];
     __shared__ int s_tile;
@@ -630,43 +646,51 @@ __global__ void __launch_bounds__(BLOCK_THREADS, PC_BLOCKS_OF(PREC))
         }
         const int local = t - fr[lo].tile_begin, tiles_x = fr[lo].tiles_x;
         const int ty_ = local / tiles_x;
-        fit_tile<RW, REJECT, PREC>(fr[lo].f, cfg, local - ty_ * tiles_x, ty_, smem);
+        fit_tile<RW, REJECT, PREC, TH>(fr[lo].f, cfg, local - ty_ * tiles_x, ty_, smem);
         __syncthreads();  // shared memory and s_tile are reused by the next tile
     }
 }
 
-template <int RW, int PREC = 0>
+template <int RW, int PREC, int TH>
 cudaError_t launch_fit_rw(const FrameArgs& f, const FitConfig& cfg, cudaStream_t stream) {
-    const dim3 block(TILE_W, TILE_H);
-    const dim3 grid((f.W + TILE_W - 1) / TILE_W, (f.H + TILE_H - 1) / TILE_H);
-    const size_t smem = fit_smem_bytes(cfg);
+    const dim3 block(TILE_W, TH);
+    const dim3 grid((f.W + TILE_W - 1) / TILE_W, (f.H + TH - 1) / TH);
+    const size_t smem = fit_smem_bytes(cfg, TH);
     if (cfg.reject)
-        k_fit<RW, true, PREC><<<grid, block, smem, stream>>>(f, cfg);
+        k_fit<RW, true, PREC, TH><<<grid, block, smem, stream>>>(f, cfg);
     else
-        k_fit<RW, false, PREC><<<grid, block, smem, stream>>>(f, cfg);
+        k_fit<RW, false, PREC, TH><<<grid, block, smem, stream>>>(f, cfg);
     return cudaGetLastError();
 }
 
-template <int RW, int PREC = 0>
+template <int RW, int PREC, int TH>
 cudaError_t launch_batch_rw(const BatchTable* table, unsigned* next_tile, int grid, const FitConfig& cfg,
                             cudaStream_t stream) {
-    const dim3 block(TILE_W, TILE_H);
-    const size_t smem = fit_smem_bytes(cfg);
+    const dim3 block(TILE_W, TH);
+    const size_t smem = fit_smem_bytes(cfg, TH);
     if (cfg.reject)
-        k_fit_batch<RW, true, PREC><<<grid, block, smem, stream>>>(table, next_tile, cfg);
+        k_fit_batch<RW, true, PREC, TH><<<grid, block, smem, stream>>>(table, next_tile, cfg);
     else
-        k_fit_batch<RW, false, PREC><<<grid, block, smem, stream>>>(table, next_tile, cfg);
+        k_fit_batch<RW, false, PREC, TH><<<grid, block, smem, stream>>>(table, next_tile, cfg);
     return cudaGetLastError();
 }
 
-template <int RW, int PREC = 0>
+template <int RW, int PREC, int TH>
 cudaError_t occupancy_rw(const FitConfig& cfg, int* blocks_per_sm) {
-    const size_t smem = fit_smem_bytes(cfg);
-    return cfg.reject
-               ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fit_batch<RW, true, PREC>,
-                                                               BLOCK_THREADS, smem)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fit_batch<RW, false, PREC>,
-                                                               BLOCK_THREADS, smem);
+    const size_t smem = fit_smem_bytes(cfg, TH);
+    return cfg.reject ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            blocks_per_sm, k_fit_batch<RW, true, PREC, TH>, TILE_W * TH, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            blocks_per_sm, k_fit_batch<RW, false, PREC, TH>, TILE_W * TH, smem);
+}
+
+// The op table of radius RW (RW = 0: run-time radius) for both tile variants.
+template <int RW, int PREC>
+const KernelOps* make_ops() {
+    static const KernelOps k = {{launch_fit_rw<RW, PREC, 8>, launch_fit_rw<RW, PREC, 4>},
+                                {launch_batch_rw<RW, PREC, 8>, launch_batch_rw<RW, PREC, 4>},
+                                {occupancy_rw<RW, PREC, 8>, occupancy_rw<RW, PREC, 4>}};
+    return &k;
 }
 
 }  // namespace pcurv

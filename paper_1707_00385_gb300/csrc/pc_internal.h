@@ -27,18 +27,26 @@ struct FitConfig {
     float fp64_pivot;  // refactorise in FP64 below this scaled pivot (0 = never)
 };
 
-// Output tile of one CTA: TILE_W x TILE_H pixels, one thread per pixel.
+// Output tile of one CTA: TILE_W x th pixels, one thread per pixel, in two
+// variants (th = 8: 256 threads; th = 4: 128 threads, for frames with few
+// tiles).  The per-pixel arithmetic does not depend on the variant.
 constexpr int TILE_W = 32;
-constexpr int TILE_H = 8;
-constexpr int BLOCK_THREADS = TILE_W * TILE_H;
+constexpr int NUM_TILE_VARIANTS = 2;
+inline int tile_h_of(int variant) { return variant == 1 ? 4 : 8; }
+// storage tiles of the 16-bit range format (pc_pack_depth): 32 x 8
+constexpr int PACK_TILE_H = 8;
 
 inline int halo_of(const FitConfig& c) { return c.r > c.rn ? c.r : c.rn; }
 
 // Z and c planes of the tile + halo, and per-row valid counts.
-inline size_t fit_smem_bytes(const FitConfig& c) {
+inline size_t fit_smem_bytes(const FitConfig& c, int th) {
     const int h = halo_of(c);
-    return (size_t)(TILE_W + 2 * h) * (TILE_H + 2 * h) * 2 * sizeof(float) +
-           (size_t)(TILE_H + 2 * h) * TILE_W * sizeof(int);
+    return (size_t)(TILE_W + 2 * h) * (th + 2 * h) * 2 * sizeof(float) +
+           (size_t)(th + 2 * h) * TILE_W * sizeof(int);
+}
+
+inline long long tiles_of(int H, int W, int th) {
+    return (long long)((W + TILE_W - 1) / TILE_W) * ((H + th - 1) / th);
 }
 
 // One frame: caller-owned device buffers, size and intrinsics.
@@ -74,11 +82,12 @@ inline size_t batch_table_bytes(int nframes) {
     return sizeof(BatchTable) + (size_t)(nframes > 1 ? nframes - 1 : 0) * sizeof(BatchFrame);
 }
 
-// Kernel entry points of one instantiation (window radius, dense or run-time).
+// Kernel entry points of one instantiation (window radius, dense or run-time),
+// per tile variant (nullptr where a variant is not compiled).
 struct KernelOps {
-    cudaError_t (*fit)(const FrameArgs&, const FitConfig&, cudaStream_t);
-    cudaError_t (*batch)(const BatchTable*, unsigned*, int, const FitConfig&, cudaStream_t);
-    cudaError_t (*occupancy)(const FitConfig&, int*);
+    cudaError_t (*fit[NUM_TILE_VARIANTS])(const FrameArgs&, const FitConfig&, cudaStream_t);
+    cudaError_t (*batch[NUM_TILE_VARIANTS])(const BatchTable*, unsigned*, int, const FitConfig&, cudaStream_t);
+    cudaError_t (*occupancy[NUM_TILE_VARIANTS])(const FitConfig&, int*);
 };
 
 // Instantiation groups (one translation unit each, compiled in parallel);

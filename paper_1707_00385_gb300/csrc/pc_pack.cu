@@ -12,11 +12,13 @@
 
 namespace pcurv {
 
-__global__ void __launch_bounds__(BLOCK_THREADS)
+constexpr int PACK_THREADS = TILE_W * PACK_TILE_H;
+
+__global__ void __launch_bounds__(PACK_THREADS)
     k_pack(const float* __restrict__ depth, int H, int W, int format, unsigned short* __restrict__ packed,
            float* __restrict__ tile_base) {
-    __shared__ float s_lo[BLOCK_THREADS / 32], s_hi[BLOCK_THREADS / 32];
-    const int u = blockIdx.x * TILE_W + threadIdx.x, v = blockIdx.y * TILE_H + threadIdx.y;
+    __shared__ float s_lo[PACK_THREADS / 32], s_hi[PACK_THREADS / 32];
+    const int u = blockIdx.x * TILE_W + threadIdx.x, v = blockIdx.y * PACK_TILE_H + threadIdx.y;
     const int tid = threadIdx.y * TILE_W + threadIdx.x;
     const bool inside = u < W && v < H;
     const float d = inside ? depth[(size_t)v * W + u] : 0.f;
@@ -35,7 +37,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS)
     lo = s_lo[0];
     hi = s_hi[0];
 #pragma unroll
-    for (int i = 1; i < BLOCK_THREADS / 32; i++) {
+    for (int i = 1; i < PACK_THREADS / 32; i++) {
         lo = fminf(lo, s_lo[i]);
         hi = fmaxf(hi, s_hi[i]);
     }
@@ -49,8 +51,8 @@ __global__ void __launch_bounds__(BLOCK_THREADS)
 
 cudaError_t launch_pack(const float* depth, int H, int W, int format, unsigned short* packed,
                         float* tile_base, cudaStream_t stream) {
-    const dim3 block(TILE_W, TILE_H);
-    const dim3 grid((W + TILE_W - 1) / TILE_W, (H + TILE_H - 1) / TILE_H);
+    const dim3 block(TILE_W, PACK_TILE_H);
+    const dim3 grid((W + TILE_W - 1) / TILE_W, (H + PACK_TILE_H - 1) / PACK_TILE_H);
     k_pack<<<grid, block, 0, stream>>>(depth, H, W, format, packed, tile_base);
     return cudaGetLastError();
 }

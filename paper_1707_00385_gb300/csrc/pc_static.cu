@@ -23,6 +23,7 @@ constexpr size_t kTableBytes =
     (sizeof(pcurv::BatchTable) + (kMaxFrames - 1) * sizeof(pcurv::BatchFrame) + 255) / 256 * 256;
 constexpr size_t kScratchBytes = kCounterBytes + kTableBytes;
 constexpr int kMaxDevices = 64;
+constexpr int kTileH = 8;  // this entry point always runs the 32 x 8 tile variant
 
 static __device__ __align__(256) unsigned char pc_static_scratch[kScratchBytes];
 
@@ -76,8 +77,7 @@ extern "C" pc_status pc_compute_batch_static(pc_ctx* ctx, const pc_frame* frames
         if (f.H < 0 || f.W < 0 || f.H > PC_MAX_DIM || f.W > PC_MAX_DIM) return PC_ERR_INVALID_ARG;
         if (f.H == 0 || f.W == 0) continue;
         if (!ok_intrinsics(f) || !ok_buffers(f)) return PC_ERR_INVALID_ARG;
-        total += (long long)((f.W + pcurv::TILE_W - 1) / pcurv::TILE_W) *
-                 ((f.H + pcurv::TILE_H - 1) / pcurv::TILE_H);
+        total += pcurv::tiles_of(f.H, f.W, kTileH);
         live++;
     }
     if (live == 0) return PC_OK;
@@ -91,7 +91,7 @@ extern "C" pc_status pc_compute_batch_static(pc_ctx* ctx, const pc_frame* frames
     const pcurv::KernelOps* ops = pcurv::select_ops(cfg);
     int sms = 0, bps = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-        (e = ops->occupancy(cfg, &bps)) != cudaSuccess)
+        (e = ops->occupancy[0](cfg, &bps)) != cudaSuccess)
         return fail(ctx, PC_ERR_CUDA, "occupancy", e);
 
     std::lock_guard<std::mutex> lock(g_mu);
@@ -116,7 +116,7 @@ extern "C" pc_status pc_compute_batch_static(pc_ctx* ctx, const pc_frame* frames
                                f.k1, f.k2, f.normal, nullptr, nullptr};
         d.tiles_x = (f.W + pcurv::TILE_W - 1) / pcurv::TILE_W;
         d.tile_begin = begin;
-        begin += d.tiles_x * ((f.H + pcurv::TILE_H - 1) / pcurv::TILE_H);
+        begin += d.tiles_x * ((f.H + kTileH - 1) / kTileH);
     }
     t->nframes = live;
     t->total_tiles = begin;
@@ -128,7 +128,7 @@ extern "C" pc_status pc_compute_batch_static(pc_ctx* ctx, const pc_frame* frames
         return fail(ctx, PC_ERR_CUDA, "frame table copy", e);
     if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s)) != cudaSuccess)
         return fail(ctx, PC_ERR_CUDA, "counter reset", e);
-    if ((e = ops->batch(table, counter, sms * (bps > 0 ? bps : 1), cfg, s)) != cudaSuccess)
+    if ((e = ops->batch[0](table, counter, sms * (bps > 0 ? bps : 1), cfg, s)) != cudaSuccess)
         return fail(ctx, PC_ERR_CUDA, "launch", e);
     return PC_OK;
 }

@@ -35,6 +35,7 @@ class pc_params(ctypes.Structure):
         ("batch_graph", ctypes.c_int),
         ("kahan", ctypes.c_int),
         ("fp64_solve_cond", ctypes.c_float),
+        ("tile_height", ctypes.c_int),
     ]
 
 
@@ -75,6 +76,9 @@ def load() -> ctypes.CDLL:
         L.pc_compute_batch.argtypes = [_vp, ctypes.POINTER(pc_frame), ctypes.c_int, _vp]
         L.pc_compute_batch_static.argtypes = [_vp, ctypes.POINTER(pc_frame), ctypes.c_int, _vp]
         L.pc_pack_depth.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+        L.pc_autotune.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.pc_plan_tile_height.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+        L.pc_plan_tile_height.restype = ctypes.c_int
         L.pc_compute_packed.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                         _vp, _vp, _vp]
         L.pc_destroy.argtypes = [_vp]
@@ -83,7 +87,7 @@ def load() -> ctypes.CDLL:
         L.pc_last_error.argtypes = [_vp]
         L.pc_last_error.restype = ctypes.c_char_p
         for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_compute_batch",
-                  "pc_compute_batch_static", "pc_pack_depth", "pc_compute_packed", "pc_destroy"):
+                  "pc_compute_batch_static", "pc_pack_depth", "pc_compute_packed", "pc_autotune", "pc_destroy"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -129,6 +133,14 @@ def pc_pack_depth(ctx, depth, H, W, fmt, stream, packed, tile_base) -> int:
 
 def pc_compute_packed(ctx, packed, tile_base, fmt, H, W, stream, k1_out, k2_out, normal_out) -> int:
     return load().pc_compute_packed(ctx, packed, tile_base, fmt, H, W, stream, k1_out, k2_out, normal_out)
+
+
+def pc_autotune(ctx, depth, H, W, stream, k1_out, k2_out, normal_out) -> int:
+    return load().pc_autotune(ctx, depth, H, W, stream, k1_out, k2_out, normal_out)
+
+
+def pc_plan_tile_height(ctx, H, W) -> int:
+    return load().pc_plan_tile_height(ctx, H, W)
 
 
 def pc_destroy(ctx) -> int:
@@ -205,6 +217,23 @@ class Curvature:
         if st != PC_OK:
             raise PcError(st, "pc_compute", pc_last_error(self.ctx))
         return k1, k2, normal
+
+    def autotune(self, depth, stream=None):
+        """pc_autotune on this image: times the tile shapes, remembers the
+        fastest for its size; returns the tile height now planned."""
+        import torch
+        H, W = depth.shape
+        k1 = torch.empty((H, W), device=depth.device)
+        k2 = torch.empty((H, W), device=depth.device)
+        n = torch.empty((H, W, 3), device=depth.device)
+        st = pc_autotune(self.ctx, depth.contiguous().data_ptr(), H, W, _stream_handle(stream), k1.data_ptr(),
+                         k2.data_ptr(), n.data_ptr())
+        if st != PC_OK:
+            raise PcError(st, "pc_autotune", pc_last_error(self.ctx))
+        return pc_plan_tile_height(self.ctx, H, W)
+
+    def tile_height(self, H, W):
+        return pc_plan_tile_height(self.ctx, H, W)
 
     def batch(self, frames, stream=None):
         """pc_compute_batch over a list of (depth, (fx, fy, cx, cy), k1, k2, normal)

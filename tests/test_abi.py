@@ -99,7 +99,7 @@ def test_defaults(pc):
     assert p.k == pytest.approx(1e-4) and p.reject == 0 and p.reject_ratio == 2.0
     assert p.normal_radius == 3 and p.stride == 1 and p.min_window == 6
     assert p.pivot_tol == pytest.approx(1e-5) and p.det_tol == pytest.approx(1e-6)
-    assert p.batch_graph == 1 and p.kahan == 0 and p.fp64_solve_cond == 0.0
+    assert p.batch_graph == 1 and p.kahan == 0 and p.fp64_solve_cond == 0.0 and p.tile_height == 0
 
 
 def test_status_strings(pc):
@@ -123,7 +123,8 @@ def test_create_rejects_bad_arguments(pc, args):
                                          ("reject_ratio", 0.0), ("normal_radius", 0),
                                          ("normal_radius", 9), ("stride", 0), ("min_window", 5),
                                          ("pivot_tol", -1.0), ("det_tol", float("inf")),
-                                         ("batch_graph", 2), ("kahan", 3), ("fp64_solve_cond", -1.0)])
+                                         ("batch_graph", 2), ("kahan", 3), ("fp64_solve_cond", -1.0),
+                                         ("tile_height", 5), ("tile_height", 16)])
 def test_create_rejects_bad_params(pc, field, value):
     p = pc.pc_params_default()
     setattr(p, field, value)
@@ -163,6 +164,25 @@ def test_pack_argument_checks_without_gpu(pc):
         assert pc.pc_compute_packed(ctx, None, None, 0, 4, 4, None, None, None, None) == pc.PC_ERR_INVALID_ARG
         assert pc.pc_compute_packed(ctx, None, None, 2, 4, 4, None, None, None, None) == pc.PC_ERR_INVALID_ARG
         assert pc.pc_compute_packed(ctx, None, None, 2, 4, 0, None, None, None, None) == pc.PC_OK
+    finally:
+        pc.pc_destroy(ctx)
+
+
+def test_plan_and_autotune_argument_checks_without_gpu(pc):
+    assert pc.pc_plan_tile_height(None, 10, 10) == 0
+    st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5)
+    try:
+        assert pc.pc_plan_tile_height(ctx, -1, 10) == 0
+        assert pc.pc_autotune(ctx, None, 0, 4, None, None, None, None) == pc.PC_OK
+        assert pc.pc_autotune(ctx, None, 4, 4, None, None, None, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_autotune(None, None, 4, 4, None, None, None, None) == pc.PC_ERR_INVALID_ARG
+    finally:
+        pc.pc_destroy(ctx)
+    p = pc.pc_params_default()
+    p.tile_height = 4
+    st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5, p)
+    try:
+        assert pc.pc_plan_tile_height(ctx, 480, 640) == 4      # forced: no GPU query needed
     finally:
         pc.pc_destroy(ctx)
 
