@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--report", choices=["precision", "serve"], default=None,
+    ap.add_argument("--report", choices=["precision", "serve", "accuracy"], default=None,
                     help="instead of the benchmark line, print the error of each precision variant "
                          "against the FP64 oracle (one 640x480 frame, radii 3, 7, 11)")
     return ap.parse_args()
@@ -260,6 +260,76 @@ def serve_trace(scenes_, n, rate, seed, batched=True, plain=True):
     return out
 
 
+def _interior(mask, r):
+    """pixels whose whole (2r+1)^2 window lies inside mask (edges and corners
+    excluded, as the paper's evaluation removes them)"""
+    m = mask.astype(np.int64)
+    c = np.pad(m, ((1, 0), (1, 0))).cumsum(0).cumsum(1)
+    Hh, Ww = m.shape
+    y0, y1 = np.clip(np.arange(Hh) - r, 0, Hh), np.clip(np.arange(Hh) + r + 1, 0, Hh)
+    x0, x1 = np.clip(np.arange(Ww) - r, 0, Ww), np.clip(np.arange(Ww) + r + 1, 0, Ww)
+    box = c[y1][:, x1] - c[y0][:, x1] - c[y1][:, x0] + c[y0][:, x0]
+    return mask & (box == (2 * r + 1) ** 2)
+
+
+def accuracy_report(args):
+    """Accuracy of the method itself against analytic ground truth (GPU path):
+    the synthetic rows of the paper's Table 1 (sphere 10 cm, cylinder 9 cm,
+    torus 10/3 cm), curvature error against depth noise on a 100 mm sphere,
+    and the angular error of the refined normal against the initial one."""
+    import torch
+    import synth
+    import paper_1707_00385_gb300 as pc
+    from paper_1707_00385_gb300 import build as pcbuild
+    pcbuild.build()
+    cam = synth.kinect_camera(480, 640)
+    wall = synth.Plane(np.array([0.0, 0.0, 1.0]), 1.5)
+
+    def run(scene, r, T=5, **kw):
+        c = pc.Curvature(*scene.intrinsics, window_radius=r, iterations=T, **kw)
+        k1, k2, n = c(torch.from_numpy(scene.depth).cuda())
+        torch.cuda.synchronize()
+        c.close()
+        return k1.cpu().numpy(), k2.cpu().numpy(), n.cpu().numpy()
+
+    objects = {
+        "sphere_10cm": synth.Sphere(np.array([0.0, 0.0, 0.8]), 0.10),
+        "cylinder_9cm": synth.Cylinder(np.array([0.0, 0.0, 0.8]), np.array([0.0, 1.0, 0.0]), 0.09, 0.4),
+        "torus_10_3cm": synth.Torus(np.array([0.0, 0.0, 0.8]), np.array([0.0, -0.6, -0.8]), 0.10, 0.03),
+    }
+    windows = [("r7_dense", 7, 1), ("37x37_stride3", 18, 3)]
+    for noise_name, noise in (("none", None), ("kinect", synth.kinect_noise)):
+        for name, obj in objects.items():
+            sc = synth.render(cam, [obj, wall], noise=noise, rng=np.random.default_rng(1))
+            for wname, r, st in windows:
+                k1, k2, _ = run(sc, r, stride=st)
+                m = _interior(sc.label == 0, r) & np.isfinite(k1)
+                e = np.concatenate([(k1 - sc.gt_k1)[m], (k2 - sc.gt_k2)[m]]) / 1000.0   # mm^-1
+                print(json.dumps({"table1_row": name, "noise": noise_name, "window": wname, "pixels": int(m.sum()),
+                                  "expected_k_per_mm": [float(np.nanmean(sc.gt_k1[m]) / 1000), float(np.nanmean(sc.gt_k2[m]) / 1000)],
+                                  "computed_k_per_mm": [float(np.mean(k1[m]) / 1000), float(np.mean(k2[m]) / 1000)],
+                                  "rms_per_mm": float(np.sqrt(np.mean(e * e))), "sigma_per_mm": float(np.std(e))}),
+                      flush=True)
+    sph = objects["sphere_10cm"]
+    for sigma_mm in (0.0, 0.5, 1.0, 2.0, 3.0, 4.0, 5.0):
+        sc = synth.render(cam, [sph, wall], noise=synth.const_noise(sigma_mm * 1e-3) if sigma_mm else None,
+                          rng=np.random.default_rng(2))
+        row = {"noise_mm": sigma_mm}
+        for tag, kw in (("ours", {}), ("ours_rejection", {"reject": 1})):
+            k1, k2, n = run(sc, 7, **kw)
+            m = _interior(sc.label == 0, 7) & np.isfinite(k1)
+            e = np.concatenate([(k1 - 10.0)[m], (k2 - 10.0)[m]])
+            row[tag + "_rms_per_m"] = float(np.sqrt(np.mean(e * e)))
+            if tag == "ours":
+                ang = np.degrees(np.arccos(np.clip(np.sum(n[m] * sc.gt_normal[m], -1), -1, 1)))
+                row["refined_normal_mean_deg"] = float(np.mean(ang))
+        _, _, n0 = run(sc, 7, T=0)
+        m = _interior(sc.label == 0, 7) & np.isfinite(n0[..., 0])
+        ang0 = np.degrees(np.arccos(np.clip(np.sum(n0[m] * sc.gt_normal[m], -1), -1, 1)))
+        row["initial_normal_mean_deg"] = float(np.mean(ang0))
+        print(json.dumps({"sphere_100mm_vs_noise": row}), flush=True)
+
+
 def precision_report(args):
     """Error of each precision variant against the FP64 oracle on one seeded
     640x480 Kinect-like frame, per window radius, with its time per frame."""
@@ -316,6 +386,9 @@ def main():
     args = parse()
     if args.report == "precision":
         precision_report(args)
+        return
+    if args.report == "accuracy":
+        accuracy_report(args)
         return
     if args.report == "serve":
         # SURVEY config 5: 20,000 requests at 2,000/s, then a point at half the

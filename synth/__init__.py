@@ -199,6 +199,69 @@ class Saddle:
         return t, k1, k2, nrm
 
 
+@dataclass
+class Torus:
+    """torus around axis e (unit) through centre c: ring radius R, tube radius rho"""
+    c: np.ndarray
+    e: np.ndarray
+    R: float
+    rho: float
+
+    def _parts(self, P):
+        q = P - self.c
+        s = q @ self.e
+        radial = q - s[..., None] * self.e
+        dr = np.linalg.norm(radial, axis=-1)
+        return q, s, radial, dr
+
+    def hit(self, rays):
+        d = rays / np.linalg.norm(rays, axis=-1, keepdims=True)
+        scale = np.linalg.norm(rays, axis=-1)
+        bound = self.R + self.rho
+        # start at the bounding sphere, march by the exact distance (sphere tracing)
+        dc = d @ self.c
+        disc = dc * dc - (self.c @ self.c - bound * bound)
+        t = np.where(disc > 0, dc - np.sqrt(np.maximum(disc, 0.0)), np.inf)
+        t = np.maximum(t, 0.0)
+        t_far = np.where(disc > 0, dc + np.sqrt(np.maximum(disc, 0.0)), -np.inf)
+        alive = np.isfinite(t)
+        for _ in range(400):
+            P = d * np.where(alive, t, 0.0)[..., None]
+            _, s_, _, dr = self._parts(P)
+            sdf = np.sqrt((dr - self.R) ** 2 + s_ ** 2) - self.rho
+            step = np.where(alive, sdf, 0.0)
+            t = t + step
+            alive &= (np.abs(sdf) > 1e-12) & (t <= t_far)
+        P = d * np.where(np.isfinite(t), t, 0.0)[..., None]
+        _, s_, _, dr = self._parts(P)
+        sdf = np.sqrt((dr - self.R) ** 2 + s_ ** 2) - self.rho
+        found = np.isfinite(t) & (np.abs(sdf) < 1e-9) & (t <= t_far + 1e-9)
+        # Newton on the quartic F = (|q|^2 + R^2 - rho^2)^2 - 4 R^2 (|q|^2 - s^2) along the ray
+        for _ in range(3):
+            P = d * np.where(found, t, 0.0)[..., None]
+            q, s_, _, _ = self._parts(P)
+            qq = np.einsum("...i,...i->...", q, q)
+            g = qq + self.R ** 2 - self.rho ** 2
+            F = g * g - 4 * self.R ** 2 * (qq - s_ * s_)
+            dqq = 2 * (q @ np.eye(3) * d).sum(-1)
+            ds = d @ self.e
+            dF = 2 * g * dqq - 4 * self.R ** 2 * (dqq - 2 * s_ * ds)
+            t = np.where(found & (dF != 0), t - F / np.where(dF != 0, dF, 1.0), t)
+        z = np.where(found, t / scale, np.inf)     # ray parameter of the unnormalised ray = depth
+        P = rays * np.where(found, z, 0.0)[..., None]
+        q, s_, radial, dr = self._parts(P)
+        cosphi = (dr - self.R) / self.rho
+        ring_dir = radial / np.maximum(dr, 1e-300)[..., None]
+        outward = ((dr - self.R)[..., None] * ring_dir + s_[..., None] * self.e) / self.rho
+        nrm = _away(outward, rays)
+        kt = np.full(z.shape, 1.0 / self.rho)
+        kr = cosphi / (self.R + self.rho * cosphi)
+        # seen from outside: convex towards the camera is positive
+        k1 = np.where(found, np.maximum(kt, kr), np.nan)
+        k2 = np.where(found, np.minimum(kt, kr), np.nan)
+        return z, k1, k2, nrm
+
+
 # ---------------------------------------------------------------------------
 
 @dataclass

@@ -32,3 +32,20 @@ def test_sphere_scene_ground_truth():
     assert s.clean[24, 32] == pytest.approx(0.7)
     assert s.clean[0, 0] == pytest.approx(1.5)
     assert abs(float(s.depth[0, 0]) - 1.5) < 0.006    # 1 mm noise
+
+
+def test_torus_hits_lie_on_the_surface_with_analytic_curvature():
+    cam = synth.Camera(60, 80, 100.0, 100.0, 39.5, 29.5)
+    tor = synth.Torus(np.array([0.0, 0.0, 0.8]), np.array([0.0, -0.6, -0.8]), 0.10, 0.03)
+    z, k1, k2, n = tor.hit(cam.rays())
+    ok = np.isfinite(z)
+    assert ok.sum() > 100
+    P = cam.rays() * np.where(ok, z, 0.0)[..., None]
+    q = P - tor.c
+    s = q @ tor.e
+    dr = np.linalg.norm(q - s[..., None] * tor.e, axis=-1)
+    assert np.abs(np.sqrt((dr - tor.R) ** 2 + s ** 2) - tor.rho)[ok].max() < 1e-12
+    # tube curvature 1/rho everywhere; ring curvature between the inner and outer equators
+    assert np.allclose(np.maximum(k1, k2)[ok], 1 / 0.03)
+    assert k2[ok].min() >= -1 / 0.07 - 1e-9 and k2[ok].max() <= 1 / 0.13 + 1e-9
+    assert np.allclose(np.linalg.norm(n[ok], axis=-1), 1.0)
