@@ -391,7 +391,7 @@ def main():
         accuracy_report(args)
         return
     if args.report == "serve":
-        # SURVEY config 5: 20,000 requests at 2,000/s, then a point at half the
+        # the serving workload: 20,000 requests at 2,000/s, then a point at half the
         # measured batched capacity
         un = uneven_scenes(2)
         full = serve_trace(un, args.serve_requests, args.serve_rate, seed=11)
