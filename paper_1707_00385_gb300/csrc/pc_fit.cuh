@@ -84,13 +84,18 @@ struct Moments2 {
     f32x2 g0, g1, ge, g3, g4, g5;   // sum -w eps j0, w eps j1, w eps, w eps x^2, w eps x y, w eps y^2
 };
 
-// Per-iteration constants of one pixel, splat into pairs.
+// Per-iteration constants of one pixel, splat into pairs.  With sigma = 1/sqrt(k)
+// the loop carries e = sigma eps (so the Cauchy weight is 1 / (1 + e^2)) and
+// hs = (2 / sigma) h, so that one gradient serves residual and Jacobian:
+//   ga = sigma/2 (A x + B y), gb = sigma/2 (B x + C y),
+//   e  = ga x + gb y - sigma h - sigma t_z,
+//   j1 = (A x + B y) h + x = ga hs + x,  -j0 = (B x + C y) h + y = gb hs + y.
 struct Coef2 {
-    f32x2 cx0, cx1, cx2;       // x = Z (du cx0 + dv cy0) + dZ bx, likewise y, h
+    f32x2 cx0, cx1, cx2;       // x = Z (du cx0 + dv cy0) + dZ bx, likewise y and hs
     f32x2 bx, by, bh;
-    f32x2 hA, hC, A, B, C;     // A/2, C/2, A, B, C
-    f32x2 ntz;                 // -t_z
-    f32x2 invk;                // 1/k
+    f32x2 ga, gb, gc;          // sigma/2 (A, B, C)
+    f32x2 nhs;                 // -sigma^2 / 2: -sigma h = nhs hs
+    f32x2 nts;                 // -sigma t_z
     f32x2 nzp;                 // -Z_p
 };
 
@@ -103,7 +108,8 @@ __device__ __forceinline__ void zero(Moments2& m) {
     m.g0 = m.g1 = m.ge = m.g3 = m.g4 = m.g5 = z;
 }
 
-// Local coordinates (x, y, h) of a pair.  DU = (du, -du); RX = (dv cy0, -dv cy0).
+// Local coordinates (x, y, hs) of a pair (hs = (2/sigma) h, from the scaled h row).
+// DU = (du, -du); RX = (dv cy0, -dv cy0).
 __device__ __forceinline__ void local_xyz2(const Coef2& k, f32x2 Z, f32x2 DU, f32x2 RX, f32x2 RY,
                                            f32x2 RH, f32x2& X, f32x2& Y, f32x2& Hh) {
     const f32x2 dZ = add2(Z, k.nzp);
@@ -144,54 +150,64 @@ __device__ __forceinline__ void acc_add(f32x2& s, f32x2& nc, f32x2 x) {
     }
 }
 
-// One symmetric pair: residuals (Eq. quad in the local frame), weights,
-// Jacobian rows and the 26 sums.  C = (c_a, c_b), 1 valid / +inf invalid.
+// Scaled residuals e = sigma eps of a pair (with x, y, hs).
+__device__ __forceinline__ f32x2 residual2(const Coef2& k, f32x2 X, f32x2 Y, f32x2 Hs, f32x2& GA,
+                                          f32x2& GB) {
+    GA = fma2(k.ga, X, mul2(k.gb, Y));
+    GB = fma2(k.gb, X, mul2(k.gc, Y));
+    return fma2(GA, X, fma2(GB, Y, fma2(k.nhs, Hs, k.nts)));
+}
+
+// One symmetric pair: residuals (the quadric of Sec. 3.2 in the local frame),
+// Cauchy weights, Jacobian rows and the 26 sums (the eps sums scaled by sigma).
+// C = (c_a, c_b), 1 valid / +inf invalid.  thr bounds e^2 when REJECT.
 // c holds the compensations of the sums when KAHAN (unused otherwise).
-template <bool REJECT, bool KAHAN>
+// FIRST: the first iteration, where A = B = C = 0, so that e = -sigma (h + t_z),
+// j1 = x, -j0 = y, and five sums repeat others (first_iteration_sums fills them).
+template <bool REJECT, bool KAHAN, bool FIRST>
 __device__ __forceinline__ void visit2(Moments2& m, Moments2& c, const Coef2& k, float za, float zb,
                                        float ca, float cb, f32x2 DU, f32x2 RX, f32x2 RY, f32x2 RH,
                                        float thr) {
-    const f32x2 Z = pack(za, zb);
-    f32x2 X, Y, Hh;
-    local_xyz2(k, Z, DU, RX, RY, RH, X, Y, Hh);
-    const f32x2 XX = mul2(X, X), XY = mul2(X, Y), YY = mul2(Y, Y);
-    // eps = A/2 x^2 + B x y + C/2 y^2 - t_z - h
-    const f32x2 EPS = sub2(fma2(k.hA, XX, fma2(k.B, XY, fma2(k.hC, YY, k.ntz))), Hh);
-    const f32x2 E2 = mul2(EPS, EPS);
+    f32x2 X, Y, Hs, GA, GB;
+    local_xyz2(k, pack(za, zb), DU, RX, RY, RH, X, Y, Hs);
+    const f32x2 E = FIRST ? fma2(k.nhs, Hs, k.nts) : residual2(k, X, Y, Hs, GA, GB);
     float da, db;
-    unpack(fma2(E2, k.invk, pack(ca, cb)), da, db);
+    unpack(fma2(E, E, pack(ca, cb)), da, db);
     float wa = rcp_approx(da), wb = rcp_approx(db);
     if (REJECT) {
         float ea, eb;
-        unpack(E2, ea, eb);
+        unpack(mul2(E, E), ea, eb);
         wa = ea <= thr ? wa : 0.f;
         wb = eb <= thr ? wb : 0.f;
     }
     const f32x2 Wt = pack(wa, wb);
-    // -j0 = (B x + C y) h + y ; j1 = (A x + B y) h + x
-    const f32x2 NJ0 = fma2(fma2(k.B, X, mul2(k.C, Y)), Hh, Y);
-    const f32x2 J1 = fma2(fma2(k.A, X, mul2(k.B, Y)), Hh, X);
-    const f32x2 WE = mul2(Wt, EPS), WJ0 = mul2(Wt, NJ0), WJ1 = mul2(Wt, J1);
-    const f32x2 WXX = mul2(Wt, XX), WXY = mul2(Wt, XY), WYY = mul2(Wt, YY);
-    acc_fma<KAHAN>(m.h00, c.h00, WJ0, NJ0);
-    acc_fma<KAHAN>(m.h01, c.h01, WJ0, J1);
-    acc_fma<KAHAN>(m.h11, c.h11, WJ1, J1);
+    const f32x2 NJ0 = FIRST ? Y : fma2(GB, Hs, Y);
+    const f32x2 J1 = FIRST ? X : fma2(GA, Hs, X);
+    const f32x2 XX = mul2(X, X), XY = mul2(X, Y), YY = mul2(Y, Y);
+    const f32x2 WE = mul2(Wt, E), WJ0 = mul2(Wt, NJ0), WJ1 = mul2(Wt, J1);
+    const f32x2 WXX = mul2(Wt, XX), WYY = mul2(Wt, YY);
+    if (!FIRST) {
+        // with j1 = x, -j0 = y these are sum w y^2, w x y, w x^2, w x^2 y, w x y^2
+        acc_fma<KAHAN>(m.h00, c.h00, WJ0, NJ0);
+        acc_fma<KAHAN>(m.h01, c.h01, WJ0, J1);
+        acc_fma<KAHAN>(m.h11, c.h11, WJ1, J1);
+        acc_fma<KAHAN>(m.h14, c.h14, WJ1, XY);
+        acc_fma<KAHAN>(m.h15, c.h15, WJ1, YY);
+    }
     acc_add<KAHAN>(m.s0, c.s0, WJ0);
     acc_add<KAHAN>(m.s1, c.s1, WJ1);
     acc_fma<KAHAN>(m.h03, c.h03, WJ0, XX);
     acc_fma<KAHAN>(m.h04, c.h04, WJ0, XY);
     acc_fma<KAHAN>(m.h05, c.h05, WJ0, YY);
     acc_fma<KAHAN>(m.h13, c.h13, WJ1, XX);
-    acc_fma<KAHAN>(m.h14, c.h14, WJ1, XY);
-    acc_fma<KAHAN>(m.h15, c.h15, WJ1, YY);
     acc_add<KAHAN>(m.sw, c.sw, Wt);
     acc_add<KAHAN>(m.sxx, c.sxx, WXX);
-    acc_add<KAHAN>(m.sxy, c.sxy, WXY);
+    acc_fma<KAHAN>(m.sxy, c.sxy, Wt, XY);
     acc_add<KAHAN>(m.syy, c.syy, WYY);
     acc_fma<KAHAN>(m.m40, c.m40, WXX, XX);
     acc_fma<KAHAN>(m.m31, c.m31, WXX, XY);
     acc_fma<KAHAN>(m.m22, c.m22, WXX, YY);
-    acc_fma<KAHAN>(m.m13, c.m13, WXY, YY);
+    acc_fma<KAHAN>(m.m13, c.m13, WYY, XY);
     acc_fma<KAHAN>(m.m04, c.m04, WYY, YY);
     acc_fma<KAHAN>(m.g0, c.g0, WE, NJ0);
     acc_fma<KAHAN>(m.g1, c.g1, WE, J1);
@@ -201,14 +217,22 @@ __device__ __forceinline__ void visit2(Moments2& m, Moments2& c, const Coef2& k,
     acc_fma<KAHAN>(m.g5, c.g5, WE, YY);
 }
 
-// Squared residuals of a pair, 0 for invalid points (rejection pre-pass).
+// The sums the first iteration does not accumulate: with j1 = x and -j0 = y,
+// sum w j0 j0 = sum w y^2, -sum w j0 j1 = sum w x y, sum w j1 j1 = sum w x^2,
+// sum w j1 x y = -sum w j0 x^2 (negated convention: h03), sum w j1 y^2 = h04.
+__device__ __forceinline__ void first_iteration_sums(Moments2& m, Moments2& c) {
+    m.h00 = m.syy; m.h01 = m.sxy; m.h11 = m.sxx; m.h14 = m.h03; m.h15 = m.h04;
+    c.h00 = c.syy; c.h01 = c.sxy; c.h11 = c.sxx; c.h14 = c.h03; c.h15 = c.h04;
+}
+
+// Squared scaled residuals e^2 of a pair, 0 for invalid points (rejection pre-pass).
 __device__ __forceinline__ float sq_residual2(const Coef2& k, float za, float zb, float ca,
                                               float cb, f32x2 DU, f32x2 RX, f32x2 RY, f32x2 RH) {
-    f32x2 X, Y, Hh;
-    local_xyz2(k, pack(za, zb), DU, RX, RY, RH, X, Y, Hh);
-    const f32x2 EPS = sub2(fma2(k.hA, mul2(X, X), fma2(k.B, mul2(X, Y), fma2(k.hC, mul2(Y, Y), k.ntz))), Hh);
+    f32x2 X, Y, Hs, GA, GB;
+    local_xyz2(k, pack(za, zb), DU, RX, RY, RH, X, Y, Hs);
+    const f32x2 E = residual2(k, X, Y, Hs, GA, GB);
     float ea, eb;
-    unpack(mul2(EPS, EPS), ea, eb);
+    unpack(mul2(E, E), ea, eb);
     return (ca == 1.f ? ea : 0.f) + (cb == 1.f ? eb : 0.f);
 }
 
@@ -289,7 +313,8 @@ __device__ __forceinline__ void ldlt6(const T (&H)[6][6], const T (&g)[6], T del
 // and judged on the FP64 pivots.
 template <bool KAHAN>
 __device__ __forceinline__ bool solve_update(const Moments2& m, const Moments2& c, float wc, float ec,
-                                             float pivot_tol, float fp64_pivot, float delta[6]) {
+                                             float isig, float pivot_tol, float fp64_pivot,
+                                             float delta[6]) {
 #define PC_FOLD(f) (KAHAN ? hsum(add2(m.f, c.f)) : hsum(m.f))
     const float h00 = PC_FOLD(h00), h01 = -PC_FOLD(h01), h11 = PC_FOLD(h11);
     const float s0 = PC_FOLD(s0), s1 = PC_FOLD(s1);
@@ -299,8 +324,9 @@ __device__ __forceinline__ bool solve_update(const Moments2& m, const Moments2& 
     const float sxx = PC_FOLD(sxx), sxy = PC_FOLD(sxy), syy = PC_FOLD(syy);
     const float m40 = PC_FOLD(m40), m31 = PC_FOLD(m31), m22 = PC_FOLD(m22), m13 = PC_FOLD(m13),
                 m04 = PC_FOLD(m04);
-    const float g0 = -PC_FOLD(g0), g1 = PC_FOLD(g1), ge = fmaf(wc, ec, PC_FOLD(ge));
-    const float g3 = PC_FOLD(g3), g4 = PC_FOLD(g4), g5 = PC_FOLD(g5);
+    // the eps sums carry sigma = 1/sqrt(k): isig = sqrt(k) restores them
+    const float g0 = -PC_FOLD(g0) * isig, g1 = PC_FOLD(g1) * isig, ge = fmaf(wc, ec, PC_FOLD(ge) * isig);
+    const float g3 = PC_FOLD(g3) * isig, g4 = PC_FOLD(g4) * isig, g5 = PC_FOLD(g5) * isig;
 #undef PC_FOLD
     float H[6][6];
     H[0][0] = h00; H[0][1] = h01; H[0][2] = s0;
@@ -537,21 +563,23 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
         R[6] = nx;                     R[7] = ny;                     R[8] = nz;
     }
 
+    // sigma = 1/sqrt(k) scales the residuals carried by the loop (Coef2)
+    const float sig = sqrtf(cfg.invk), isig = 1.f / sig, hscale = 2.f * isig;
     for (int it = 0; ok && it < cfg.T; it++) {
         Coef2 k;
         const float cx0 = R[0] * cam.ifx, cy0 = R[1] * cam.ify;
         const float cx1 = R[3] * cam.ifx, cy1 = R[4] * cam.ify;
         const float cx2 = R[6] * cam.ifx, cy2 = R[7] * cam.ify;
-        k.cx0 = splat(cx0); k.cx1 = splat(cx1); k.cx2 = splat(cx2);
+        k.cx0 = splat(cx0); k.cx1 = splat(cx1); k.cx2 = splat(cx2 * hscale);
         k.bx = splat(fmaf(cx0, ap, fmaf(cy0, bp, R[2])));
         k.by = splat(fmaf(cx1, ap, fmaf(cy1, bp, R[5])));
-        k.bh = splat(fmaf(cx2, ap, fmaf(cy2, bp, R[8])));
-        k.A = splat(A); k.B = splat(B); k.C = splat(C);
-        k.hA = splat(0.5f * A); k.hC = splat(0.5f * C);
-        k.ntz = splat(-tz0);
-        k.invk = splat(cfg.invk);
+        k.bh = splat(fmaf(cx2, ap, fmaf(cy2, bp, R[8])) * hscale);
+        const float hsig = 0.5f * sig;
+        k.ga = splat(hsig * A); k.gb = splat(hsig * B); k.gc = splat(hsig * C);
+        k.nhs = splat(-0.5f * cfg.invk);
+        k.nts = splat(-sig * tz0);
         k.nzp = splat(-Zp);
-        const f32x2 CY0 = splat(cy0), CY1 = splat(cy1), CY2 = splat(cy2);
+        const f32x2 CY0 = splat(cy0), CY1 = splat(cy1), CY2 = splat(cy2 * hscale);
         // the centre point: p' = 0, so eps_c = -t_z and j_c = (0, 0, -1, 0, 0, 0)
         const float ec = -tz0;
         const float wc = rcp_approx(fmaf(ec * ec, cfg.invk, 1.f));
@@ -559,27 +587,40 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
         float thr = 0.f;
         if (REJECT) {
             // MSE of the window at this iteration; keep eps^2 <= ratio * MSE
+            // (both sides in units of k: e^2 = eps^2 / k)
             float se = 0.f;
             for_each_pair<RW>(zc, cc, SW, r, s, [&](float za, float zb, float ca, float cb, f32x2 DU,
                                                     f32x2 DV) {
                 se += sq_residual2(k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1), mul2(DV, CY2));
             });
-            se += ec * ec;
+            const float esc = -sig * tz0;
+            se += esc * esc;
             thr = cfg.reject_ratio * (se / (float)cnt);
         }
-        const float wcr = (REJECT && !(ec * ec <= thr)) ? 0.f : wc;
+        const float esc2 = (sig * tz0) * (sig * tz0);
+        const float wcr = (REJECT && !(esc2 <= thr)) ? 0.f : wc;
 
         Moments2 m, comp;
         zero(m);
         zero(comp);
-        for_each_pair<RW>(zc, cc, SW, r, s, [&](float za, float zb, float ca, float cb, f32x2 DU,
-                                                f32x2 DV) {
-            visit2<REJECT, KAHAN>(m, comp, k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1),
-                                  mul2(DV, CY2), thr);
-        });
+        if (it == 0) {
+            // A = B = C = 0 here: the cheaper first-iteration form
+            for_each_pair<RW>(zc, cc, SW, r, s, [&](float za, float zb, float ca, float cb, f32x2 DU,
+                                                    f32x2 DV) {
+                visit2<REJECT, KAHAN, true>(m, comp, k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1),
+                                            mul2(DV, CY2), thr);
+            });
+            first_iteration_sums(m, comp);
+        } else {
+            for_each_pair<RW>(zc, cc, SW, r, s, [&](float za, float zb, float ca, float cb, f32x2 DU,
+                                                    f32x2 DV) {
+                visit2<REJECT, KAHAN, false>(m, comp, k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1),
+                                             mul2(DV, CY2), thr);
+            });
+        }
 
         float dl[6];
-        if (!solve_update<KAHAN>(m, comp, wcr, ec, cfg.pivot_tol, cfg.fp64_pivot, dl)) {
+        if (!solve_update<KAHAN>(m, comp, wcr, ec, isig, cfg.pivot_tol, cfg.fp64_pivot, dl)) {
             ok = false;
             break;
         }
