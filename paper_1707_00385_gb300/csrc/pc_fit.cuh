@@ -186,35 +186,40 @@ __device__ __forceinline__ void visit2(Moments2& m, Moments2& c, const Coef2& k,
     const f32x2 XX = mul2(X, X), XY = mul2(X, Y), YY = mul2(Y, Y);
     const f32x2 WE = mul2(Wt, E), WJ0 = mul2(Wt, NJ0), WJ1 = mul2(Wt, J1);
     const f32x2 WXX = mul2(Wt, XX), WYY = mul2(Wt, YY);
+    // The sums are ordered so that each multiply-add shares an operand with the
+    // one before it: a packed FMA whose three operands are all fresh registers
+    // issues at about 0.7 of the FP32 rate, one with a repeated operand at ~0.9.
+    acc_add<KAHAN>(m.s0, c.s0, WJ0);
+    acc_add<KAHAN>(m.s1, c.s1, WJ1);
+    acc_add<KAHAN>(m.sw, c.sw, Wt);
+    acc_add<KAHAN>(m.sxx, c.sxx, WXX);
+    acc_add<KAHAN>(m.syy, c.syy, WYY);
+    acc_add<KAHAN>(m.ge, c.ge, WE);
     if (!FIRST) {
         // with j1 = x, -j0 = y these are sum w y^2, w x y, w x^2, w x^2 y, w x y^2
         acc_fma<KAHAN>(m.h00, c.h00, WJ0, NJ0);
         acc_fma<KAHAN>(m.h01, c.h01, WJ0, J1);
-        acc_fma<KAHAN>(m.h11, c.h11, WJ1, J1);
-        acc_fma<KAHAN>(m.h14, c.h14, WJ1, XY);
-        acc_fma<KAHAN>(m.h15, c.h15, WJ1, YY);
     }
-    acc_add<KAHAN>(m.s0, c.s0, WJ0);
-    acc_add<KAHAN>(m.s1, c.s1, WJ1);
     acc_fma<KAHAN>(m.h03, c.h03, WJ0, XX);
     acc_fma<KAHAN>(m.h04, c.h04, WJ0, XY);
     acc_fma<KAHAN>(m.h05, c.h05, WJ0, YY);
+    if (!FIRST) {
+        acc_fma<KAHAN>(m.h15, c.h15, WJ1, YY);
+        acc_fma<KAHAN>(m.h14, c.h14, WJ1, XY);
+    }
     acc_fma<KAHAN>(m.h13, c.h13, WJ1, XX);
-    acc_add<KAHAN>(m.sw, c.sw, Wt);
-    acc_add<KAHAN>(m.sxx, c.sxx, WXX);
-    acc_fma<KAHAN>(m.sxy, c.sxy, Wt, XY);
-    acc_add<KAHAN>(m.syy, c.syy, WYY);
-    acc_fma<KAHAN>(m.m40, c.m40, WXX, XX);
-    acc_fma<KAHAN>(m.m31, c.m31, WXX, XY);
-    acc_fma<KAHAN>(m.m22, c.m22, WXX, YY);
-    acc_fma<KAHAN>(m.m13, c.m13, WYY, XY);
-    acc_fma<KAHAN>(m.m04, c.m04, WYY, YY);
-    acc_fma<KAHAN>(m.g0, c.g0, WE, NJ0);
+    if (!FIRST) acc_fma<KAHAN>(m.h11, c.h11, WJ1, J1);
     acc_fma<KAHAN>(m.g1, c.g1, WE, J1);
-    acc_add<KAHAN>(m.ge, c.ge, WE);
+    acc_fma<KAHAN>(m.g0, c.g0, WE, NJ0);
     acc_fma<KAHAN>(m.g3, c.g3, WE, XX);
     acc_fma<KAHAN>(m.g4, c.g4, WE, XY);
     acc_fma<KAHAN>(m.g5, c.g5, WE, YY);
+    acc_fma<KAHAN>(m.m04, c.m04, WYY, YY);
+    acc_fma<KAHAN>(m.m13, c.m13, WYY, XY);
+    acc_fma<KAHAN>(m.sxy, c.sxy, Wt, XY);
+    acc_fma<KAHAN>(m.m31, c.m31, WXX, XY);
+    acc_fma<KAHAN>(m.m40, c.m40, WXX, XX);
+    acc_fma<KAHAN>(m.m22, c.m22, WXX, YY);
 }
 
 // The sums the first iteration does not accumulate: with j1 = x and -j0 = y,
