@@ -12,11 +12,14 @@ Prints one JSON line.  `value` is Mpixel/s over the device-timed region with
 inputs resident in HBM; `per_frame_launches` is the same with one pc_compute
 launch per frame; `uneven_batch` runs 64 frames of mixed resolutions
 (320x240, 512x424 time-of-flight, 640x480, 1280x720) in one batch call
-against 64 plain launches; `e2e` is the metric through pc_compute_host with
-pinned host buffers (host-to-device ranges and device-to-host k1, k2, normals
-inside the timed region); `roofline` reports the persistent kernel against
-the FP32 ALU peak; `cpu_baseline` times the FP64 oracle on a bounded sample
-on the host.
+against 64 plain launches; `e2e` is the metric through pc_compute_host_batch
+with pinned host buffers (host-to-device ranges and device-to-host k1, k2,
+normals inside the timed region, pipelined in chunks against the compute;
+`one_call_per_frame` is the unpipelined pc_compute_host); `outputs` times
+the organised point cloud (pc_backproject, against the HBM peak) and the
+initial-normal field (pc_initial_normals); `roofline` reports the persistent
+kernel against the FP32 ALU peak; `cpu_baseline` times the FP64 oracle on a
+bounded sample on the host.
 
 --impl reference times the oracle alone, on the host cores, on the same
 workload (each step a bounded sample).
@@ -108,6 +111,15 @@ def counted_flop(depth, r=RADIUS, T=ITERS, rn=3):
     nw, nn = box(r), box(rn)
     use = valid & (nw >= 6) & (nn >= 3)
     return float(np.sum(np.where(use, T * (FLOP_PER_VISIT * nw + FLOP_PER_SOLVE) + FLOP_PER_NORMAL_PT * nn, 0)))
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this GPU model (MEASURED_PEAKS.json), or None"""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def kernel_sources_hash():
@@ -523,27 +535,65 @@ def main():
     hk2 = [torch.empty((H, W)).pin_memory() for _ in range(F)]
     hn = [torch.empty((H, W, 3)).pin_memory() for _ in range(F)]
     e2e_ctx = pc.Curvature(*intr, window_radius=RADIUS, iterations=ITERS)
+    host_frames = [(hd[i], intr, hk1[i], hk2[i], hn[i]) for i in range(F)]
 
-    def step_host():
+    def step_host_batch():
+        # pipelined: chunks of frames copied in, computed and copied out on overlapping streams
+        e2e_ctx.host_batch(host_frames, stream=stream)
+        stream.synchronize()
+
+    def step_host_frames():
         for i in range(F):
             e2e_ctx.compute_host(hd[i], hk1[i], hk2[i], hn[i], stream=stream)
         stream.synchronize()
 
-    for _ in range(max(1, args.warmup)):
-        step_host()
-    barrier()
+    def wall_time(step, steps):
+        for _ in range(max(1, args.warmup)):
+            step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step()
+        t1 = time.perf_counter()
+        barrier()
+        return max_over_ranks(t1 - t0)
+
     e2e_steps = max(2, args.steps // 2)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        step_host()
-    t1 = time.perf_counter()
-    barrier()
-    e2e_s = max_over_ranks(t1 - t0)
+    e2e_s = wall_time(step_host_batch, e2e_steps)
     e2e_val = float(world) * e2e_steps * F * H * W / e2e_s / 1e6
     # host path and batched device path give the same numbers
     step_batch()
     torch.cuda.synchronize()
     same = bool(np.array_equal(hk1[0].numpy(), k1[0].cpu().numpy(), equal_nan=True))
+    e2e_pf_steps = max(1, args.steps // 4)
+    e2e_pf_val = float(world) * e2e_pf_steps * F * H * W / wall_time(step_host_frames, e2e_pf_steps) / 1e6
+
+    # ---- organised outputs (point cloud, initial-normal field) over the same frames
+    xyz = [torch.empty((H, W, 3), device=dev) for _ in range(F)]
+    n0 = [torch.empty((H, W, 3), device=dev) for _ in range(F)]
+
+    def step_backproject():
+        for i in range(F):
+            curv.backproject(depth[i], xyz[i], stream=stream)
+
+    def step_normals():
+        for i in range(F):
+            curv.initial_normals(depth[i], n0[i], stream=stream)
+
+    out_steps = max(2, args.steps // 4)
+    ms_bp = device_time(step_backproject, out_steps) / out_steps / F
+    ms_n0 = device_time(step_normals, out_steps) / out_steps / F
+    hbm_peak = measured_hbm_gbs()
+    outputs = {
+        "backproject": {"ms_per_frame": ms_bp, "mpixel_per_s": H * W / ms_bp / 1e3,
+                        "roofline": {"bound": "hbm", "achieved": 16 * H * W / (ms_bp * 1e-3) / 1e9,
+                                     "peak": hbm_peak, "unit": "GB/s",
+                                     "frac": (16 * H * W / (ms_bp * 1e-3) / 1e9 / hbm_peak) if hbm_peak else None,
+                                     "algorithmic_bytes_per_pixel": 16,
+                                     "peak_basis": "measured HBM copy bandwidth (MEASURED_PEAKS.json)"}},
+        "initial_normals": {"ms_per_frame": ms_n0, "mpixel_per_s": H * W / ms_n0 / 1e3},
+    }
+    del xyz, n0
 
     # ---- roofline of the persistent kernel: counted FP32 work vs the FP32 ALU peak
     props = torch.cuda.get_device_properties(dev)
@@ -568,8 +618,10 @@ def main():
                               f"inputs smaller than L2 ({F * H * W * 4 / 1e6:.0f} MB): profiling case only"),
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_val, "unit": "Mpixel/s", "h2d_bytes_per_step": F * H * W * 4,
-                    "d2h_bytes_per_step": F * H * W * 4 * 5, "api": "pc_compute_host",
-                    "matches_device_path": same},
+                    "d2h_bytes_per_step": F * H * W * 4 * 5, "api": "pc_compute_host_batch",
+                    "matches_device_path": same,
+                    "one_call_per_frame": {"api": "pc_compute_host", "value": e2e_pf_val, "unit": "Mpixel/s"}},
+            "outputs": outputs,
             "per_frame_launches": {"value": pf_value, "unit": "Mpixel/s", "ms_per_frame": ms_pf / max(2, args.steps // 2) / F},
             "uneven_batch": uneven,
             "serve": serve_res,

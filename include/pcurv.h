@@ -195,6 +195,46 @@ pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* str
 #define PC_STATIC_MAX_FRAMES 256
 pc_status pc_compute_batch_static(pc_ctx* ctx, const pc_frame* frames, int n, void* stream);
 
+/* The method on n frames held in HOST memory (0 <= n; the pc_frame pointers
+ * are host addresses, page-locked for the copies to overlap; normal may be
+ * NULL).  Frames are taken in order in chunks of at most
+ * PC_HOST_CHUNK_PIXELS pixels or PC_MAX_BATCH frames (a larger frame is a
+ * chunk of its own); each chunk's ranges are copied into one of two device
+ * staging slots owned by ctx, computed by one pc_compute_batch launch and its
+ * results copied back.  Copies in, computation and copies out run on three
+ * streams owned by ctx, ordered by events, so that the copies of one chunk
+ * overlap the computation of the chunks beside it.  The work starts after
+ * what is already enqueued on `stream`, and `stream` waits for the last copy
+ * out: once it is synchronised every result is on the host.  Host buffers
+ * must stay valid until then.  Results equal pc_compute's bit for bit.  The
+ * ctx's batch scratch is used on the internal compute stream: do not run
+ * pc_compute_batch on the same ctx concurrently.  Staging slots grow to the
+ * largest chunk seen (24 B per pixel each). */
+#define PC_HOST_CHUNK_PIXELS 4194304  /* 4 Mi pixels */
+pc_status pc_compute_host_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream);
+
+/* Organised point cloud of a range image: the back-projection of Sec. 3
+ * (first step of the pipeline of Sec. 3.2) written out for downstream use.
+ *   depth  device, H*W floats
+ *   xyz    device, H*W*3 floats: for pixel (u, v), u the column and v the row,
+ *          ((u - cx) Z / fx, (v - cy) Z / fy, Z) in metres, NaN where the range
+ *          is not valid (Z <= 0, infinite or NaN).  16-byte aligned buffers and
+ *          W a multiple of 4 take the vectorised path; any 4-byte aligned
+ *          buffers work.
+ * H == 0 or W == 0 is a valid empty image. */
+pc_status pc_backproject(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* xyz);
+
+/* Field of initial normals alone (Sec. 3.2.1, Eq. initialnormal): for every
+ * pixel with a valid range the least-squares plane z = a x + b y + c through
+ * the valid back-projected points of its (2 normal_radius + 1)^2 patch,
+ * normal = (-a, -b, 1) / sqrt(1 + a^2 + b^2), camera frame, n_z > 0.  NaN
+ * where the range is invalid, fewer than 3 patch points are valid or the
+ * 2x2 system is singular (det M <= det_tol (tr M)^2).  These are the normals
+ * pc_compute starts its iterations from (same arithmetic).
+ *   depth   device, H*W floats
+ *   normal  device, H*W*3 floats */
+pc_status pc_initial_normals(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* normal);
+
 /* Times the tile shapes on this image (one warm-up and three timed runs of
  * each, on `stream`, which it synchronises), remembers the fastest for images
  * of this H x W in ctx (up to 16 sizes; the oldest is forgotten first) and

@@ -101,6 +101,8 @@ def lib():
         L.or_window.argtypes = [_D, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _I, ctypes.c_int]
         L.or_fit_pixel.argtypes = [_D, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(Result)]
+        L.or_backproject_image.argtypes = [_F, ctypes.c_int, ctypes.c_int, _P, _D]
+        L.or_initial_normal_image.argtypes = [_F, ctypes.c_int, ctypes.c_int, _P, _D, _I, ctypes.c_int]
         L.or_fit_pixel_f32.argtypes = [_F, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(Result)]
         for name, dp in (("or_curvature_image", _F), ("or_curvature_image_f64", _D)):
@@ -230,6 +232,27 @@ class Field:
         th = np.hypot(self.last_b[..., 0], self.last_b[..., 1])
         with np.errstate(invalid="ignore"):
             return (self.status == OK) & (kk <= step_k * (1 + np.abs(self.k1))) & (th <= step_theta)
+
+
+def backproject_image(depth, p: Params) -> np.ndarray:
+    """Organised point cloud (H x W x 3) of a float32 range image: the
+    back-projection of every pixel, NaN where the range is not valid."""
+    d = np.ascontiguousarray(depth, dtype=np.float32)
+    H, W = d.shape
+    xyz = np.zeros((H, W, 3))
+    lib().or_backproject_image(d.ctypes.data_as(_F), H, W, ctypes.byref(p), _dp(xyz))
+    return xyz
+
+
+def initial_normal_image(depth, p: Params, nthreads: int = 0):
+    """Initial normal (H x W x 3, NaN unless OK) and status (H x W) of every
+    pixel of a float32 range image."""
+    d = np.ascontiguousarray(depth, dtype=np.float32)
+    H, W = d.shape
+    n = np.zeros((H, W, 3))
+    st = np.zeros((H, W), dtype=np.int32)
+    lib().or_initial_normal_image(d.ctypes.data_as(_F), H, W, ctypes.byref(p), _dp(n), _ip(st), nthreads)
+    return n, st
 
 
 def curvature_image(depth, p: Params, nthreads: int = 0) -> Field:

@@ -126,3 +126,79 @@ def compare(k1, k2, normal, ref: Reference, pivot_tol: float, band: float = 10.0
                   int(wp.sum()), int(np.sum(rel[wp] > 1)), float(rel[wp].max()) if wp.any() else 0.0,
                   float(np.mean(rel[both] <= 1)) if both.any() else 1.0,
                   float(ang.max()) if ang.size else 0.0, nan_ok)
+
+
+# ---- the initial-normal field on its own (Sec. 3.2.1) --------------------------
+
+NORMAL_TOL = 1e-4   # rad: angle between an implementation's normal and the oracle's
+
+
+def angle(a, b):
+    """angle (rad) between unit-ish normal fields a, b (... x 3); NaN where either is NaN"""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    c = np.sum(a * b, -1) / (np.linalg.norm(a, axis=-1) * np.linalg.norm(b, axis=-1))
+    s = np.linalg.norm(np.cross(a, b), axis=-1) / (np.linalg.norm(a, axis=-1) * np.linalg.norm(b, axis=-1))
+    return np.arctan2(s, c)
+
+
+@dataclass
+class NormalReference:
+    normal: np.ndarray   # oracle normals, H x W x 3 (NaN unless status OK)
+    status: np.ndarray
+    sens: np.ndarray     # largest angle (rad) the perturbed runs moved it; inf where validity flips
+
+
+def normal_reference(depth, p, seeds=(1, 2), nthreads=0) -> NormalReference:
+    """Oracle initial normals plus their sensitivity to relative perturbations
+    of the regression sums of size a = N u (N the patch points), as for the
+    full method."""
+    from . import initial_normal_image
+    n0, st = initial_normal_image(depth, p, nthreads)
+    npts = (2 * int(p.rn) + 1) ** 2
+    sens = np.zeros(st.shape)
+    for seed in seeds:
+        q = copy.copy(p)
+        q.perturb = npts * U
+        q.perturb_seed = seed
+        n1, st1 = initial_normal_image(depth, q, nthreads)
+        flip = (st1 == OK) != (st == OK)
+        both = (st1 == OK) & (st == OK)
+        a = np.zeros(st.shape)
+        a[both] = angle(n0[both], n1[both])
+        a[flip] = np.inf
+        sens = np.maximum(sens, a)
+    return NormalReference(n0, st, sens)
+
+
+@dataclass
+class NormalReport:
+    n_valid_oracle: int
+    n_validity_mismatch: int          # outside the sensitive set
+    n_validity_mismatch_sensitive: int
+    n_well_posed: int
+    n_well_posed_bad: int
+    max_angle_well_posed: float
+
+    def ok(self) -> bool:
+        return self.n_validity_mismatch == 0 and self.n_well_posed_bad == 0
+
+    def summary(self) -> str:
+        return (f"valid {self.n_valid_oracle}, well-posed {self.n_well_posed}, bad {self.n_well_posed_bad}, "
+                f"max angle {self.max_angle_well_posed:.3g} rad, validity mismatches "
+                f"{self.n_validity_mismatch} (+{self.n_validity_mismatch_sensitive} sensitive)")
+
+
+def compare_normals(normal, ref: NormalReference, tol: float = NORMAL_TOL) -> NormalReport:
+    """Every well-posed pixel (valid in both, oracle moved by <= tol / 4 under
+    the perturbations) within tol rad; validity agrees wherever the
+    perturbations do not flip it."""
+    g = np.asarray(normal, np.float64)
+    g_valid = np.isfinite(g).all(-1)
+    o_valid = ref.status == OK
+    mism = g_valid != o_valid
+    sensitive = ~np.isfinite(ref.sens)
+    wp = g_valid & o_valid & (ref.sens <= 0.25 * tol)
+    ang = angle(g[wp], ref.normal[wp]) if wp.any() else np.zeros(0)
+    return NormalReport(int(o_valid.sum()), int((mism & ~sensitive).sum()), int((mism & sensitive).sum()),
+                        int(wp.sum()), int((ang > tol).sum()), float(ang.max()) if ang.size else 0.0)

@@ -640,3 +640,48 @@ OR_EXPORT int or_fit_pixel_f32(const float* depth, int H, int W, const or_params
     free(d);
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* organised outputs: the back-projection and the initial normals of every   */
+/* pixel on their own (Sec. 3, Sec. 3.2.1), for the point-cloud and          */
+/* normal-field outputs                                                      */
+
+/* xyz: H*W*3, NaN where the range is not valid */
+OR_EXPORT void or_backproject_image(const float* depth, int H, int W, const or_params* p, double* xyz) {
+    const long npx = (long)H * W;
+    for (long i = 0; i < npx; i++) {
+        const double z = (double)depth[i];
+        if (!range_valid(z)) {
+            xyz[3 * i] = xyz[3 * i + 1] = xyz[3 * i + 2] = NAN;
+            continue;
+        }
+        or_backproject(p, (int)(i % W), (int)(i / W), z, xyz + 3 * i);
+    }
+}
+
+/* normal: H*W*3 (NaN unless status is OR_OK); status: H*W, OR_INVALID_CENTRE
+ * for an invalid range, OR_BAD_NORMAL when the regression fails.  With
+ * p->perturb > 0 the regression sums are perturbed under the same per-pixel
+ * keys as in or_fit_pixel. */
+OR_EXPORT void or_initial_normal_image(const float* depth, int H, int W, const or_params* p, double* normal,
+                                       int* status, int nthreads) {
+    set_threads(nthreads);
+    const long npx = (long)H * W;
+    double* d = widen(depth, npx);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long i = 0; i < npx; i++) {
+        const int u0 = (int)(i % W), v0 = (int)(i / W);
+        double* n = normal + 3 * i;
+        n[0] = n[1] = n[2] = NAN;
+        if (!range_valid(d[i])) {
+            status[i] = OR_INVALID_CENTRE;
+            continue;
+        }
+        const unsigned long long pkey =
+            splitmix64(p->perturb_seed ^ splitmix64(((unsigned long long)v0 << 32) ^ (unsigned long long)u0));
+        double m[3];
+        status[i] = initial_normal_keyed(d, H, W, p, u0, v0, m, pkey * 1024);
+        if (status[i] == OR_OK) memcpy(n, m, sizeof m);
+    }
+    free(d);
+}

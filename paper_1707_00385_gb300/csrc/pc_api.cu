@@ -32,6 +32,22 @@ struct BatchScratch {
     int next = 0;                             // staging copy of the next call
 };
 
+// Pipeline of pc_compute_host_batch: two device staging slots (each holds the
+// ranges and results of one chunk of frames) and three streams -- copies in,
+// compute, copies out -- ordered by events, so that the copies of one chunk
+// overlap the computation of its neighbours.
+struct HostPipe {
+    int device = -1;
+    cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
+    cudaEvent_t start = nullptr, tail = nullptr;
+    cudaEvent_t in_done[2] = {nullptr, nullptr}, comp_done[2] = {nullptr, nullptr};
+    cudaEvent_t slot_free[2] = {nullptr, nullptr};
+    bool slot_used[2] = {false, false};
+    float* buf[2] = {nullptr, nullptr};      // device, px * 6 floats per slot
+    size_t cap_px[2] = {0, 0};
+    pc_frame* dev_frames = nullptr;          // host: device descriptors of one chunk
+};
+
 // Tile variant chosen by pc_autotune for one image size.
 struct Plan {
     int H = 0, W = 0, variant = 0;
@@ -52,6 +68,7 @@ struct pc_ctx {
     float* d_k2 = nullptr;
     float* d_normal = nullptr;
     BatchScratch batch;
+    HostPipe pipe;
     Plan plans[16];
     long long plan_clock = 0;
     int sms_device = -1;
@@ -563,12 +580,191 @@ pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* str
     return PC_OK;
 }
 
+static void release_pipe(HostPipe& p) {
+    if (p.out) cudaStreamSynchronize(p.out);
+    for (int i = 0; i < 2; i++) {
+        cudaFree(p.buf[i]);
+        p.buf[i] = nullptr;
+        p.cap_px[i] = 0;
+        p.slot_used[i] = false;
+        for (cudaEvent_t* ev : {&p.in_done[i], &p.comp_done[i], &p.slot_free[i]}) {
+            if (*ev) cudaEventDestroy(*ev);
+            *ev = nullptr;
+        }
+    }
+    for (cudaEvent_t* ev : {&p.start, &p.tail}) {
+        if (*ev) cudaEventDestroy(*ev);
+        *ev = nullptr;
+    }
+    delete[] p.dev_frames;
+    p.dev_frames = nullptr;
+    for (cudaStream_t* st : {&p.in, &p.comp, &p.out}) {
+        if (*st) cudaStreamDestroy(*st);
+        *st = nullptr;
+    }
+    p.device = -1;
+}
+
+// Streams and events of the host pipeline on the current device.
+static pc_status ensure_pipe(pc_ctx* ctx) {
+    HostPipe& p = ctx->pipe;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetDevice");
+    if (p.device == dev) return PC_OK;
+    if (p.device >= 0) release_pipe(p);
+    p.device = dev;
+    for (cudaStream_t* st : {&p.in, &p.comp, &p.out})
+        if ((e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking)) != cudaSuccess) break;
+    for (int i = 0; i < 2 && e == cudaSuccess; i++)
+        for (cudaEvent_t* ev : {&p.in_done[i], &p.comp_done[i], &p.slot_free[i]})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    for (cudaEvent_t* ev : {&p.start, &p.tail})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        p.dev_frames = new (std::nothrow) pc_frame[PC_MAX_BATCH];
+        if (!p.dev_frames) e = cudaErrorMemoryAllocation;
+    }
+    if (e != cudaSuccess) {
+        release_pipe(p);
+        return cuda_fail(ctx, e, "pipeline streams");
+    }
+    return PC_OK;
+}
+
+pc_status pc_compute_host_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream) {
+    if (!ctx || n < 0 || (n > 0 && !frames)) return PC_ERR_INVALID_ARG;
+    size_t total_px = 0;
+    for (int i = 0; i < n; i++) {
+        const pc_frame& fr = frames[i];
+        pc_status st = check_image(fr.H, fr.W);
+        if (st != PC_OK) return st;
+        if (fr.H == 0 || fr.W == 0) continue;
+        if (!valid_intrinsics(fr.fx, fr.fy, fr.cx, fr.cy)) return PC_ERR_INVALID_ARG;
+        if (!fr.depth || !fr.k1 || !fr.k2) return PC_ERR_INVALID_ARG;
+        total_px += (size_t)fr.H * fr.W;
+    }
+    if (total_px == 0) return PC_OK;
+    pc_status st = ensure_pipe(ctx);
+    if (st != PC_OK) return st;
+    HostPipe& p = ctx->pipe;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    // start after the work the caller has already enqueued on `stream`
+    if ((e = cudaEventRecord(p.start, s)) != cudaSuccess || (e = cudaStreamWaitEvent(p.in, p.start, 0)) != cudaSuccess)
+        return cuda_fail(ctx, e, "pipeline start");
+    pc_frame* dev = p.dev_frames;
+    int i = 0, chunk = 0;
+    while (i < n) {
+        // next chunk: frames up to PC_HOST_CHUNK_PIXELS pixels (at least one frame)
+        int j = i;
+        size_t px = 0;
+        while (j < n && j - i < PC_MAX_BATCH) {
+            const size_t f = (size_t)frames[j].H * frames[j].W;
+            if (j > i && px + f > (size_t)PC_HOST_CHUNK_PIXELS) break;
+            px += f;
+            j++;
+        }
+        const int slot = chunk & 1;
+        if (px > p.cap_px[slot]) {
+            // grow: wait until the chunk that last used the slot has been copied out
+            if (p.slot_used[slot] && (e = cudaEventSynchronize(p.slot_free[slot])) != cudaSuccess)
+                return cuda_fail(ctx, e, "pipeline wait");
+            cudaFree(p.buf[slot]);
+            p.buf[slot] = nullptr;
+            p.cap_px[slot] = 0;
+            if ((e = cudaMalloc(&p.buf[slot], px * 6 * sizeof(float))) != cudaSuccess)
+                return cuda_fail(ctx, e, "pipeline cudaMalloc");
+            p.cap_px[slot] = px;
+        }
+        if (p.slot_used[slot] && (e = cudaStreamWaitEvent(p.in, p.slot_free[slot], 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "pipeline order");
+        // device layout of the slot: ranges, k1, k2 (px each), normals (3 px)
+        float* d_depth = p.buf[slot];
+        float* d_k1 = d_depth + px;
+        float* d_k2 = d_k1 + px;
+        float* d_nrm = d_k2 + px;
+        size_t off = 0;
+        int m = 0;
+        for (int q = i; q < j; q++) {
+            const pc_frame& fr = frames[q];
+            const size_t f = (size_t)fr.H * fr.W;
+            if (f == 0) continue;
+            if ((e = cudaMemcpyAsync(d_depth + off, fr.depth, f * sizeof(float), cudaMemcpyHostToDevice, p.in)) !=
+                cudaSuccess)
+                return cuda_fail(ctx, e, "pipeline H2D");
+            dev[m++] = pc_frame{d_depth + off, fr.H, fr.W, fr.fx, fr.fy, fr.cx, fr.cy, d_k1 + off, d_k2 + off,
+                                fr.normal ? d_nrm + 3 * off : nullptr};
+            off += f;
+        }
+        if ((e = cudaEventRecord(p.in_done[slot], p.in)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(p.comp, p.in_done[slot], 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "pipeline order");
+        if ((st = pc_compute_batch(ctx, dev, m, p.comp)) != PC_OK) return st;
+        if ((e = cudaEventRecord(p.comp_done[slot], p.comp)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(p.out, p.comp_done[slot], 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "pipeline order");
+        off = 0;
+        for (int q = i; q < j; q++) {
+            const pc_frame& fr = frames[q];
+            const size_t f = (size_t)fr.H * fr.W;
+            if (f == 0) continue;
+            if ((e = cudaMemcpyAsync(fr.k1, d_k1 + off, f * sizeof(float), cudaMemcpyDeviceToHost, p.out)) !=
+                    cudaSuccess ||
+                (e = cudaMemcpyAsync(fr.k2, d_k2 + off, f * sizeof(float), cudaMemcpyDeviceToHost, p.out)) !=
+                    cudaSuccess ||
+                (fr.normal && (e = cudaMemcpyAsync(fr.normal, d_nrm + 3 * off, 3 * f * sizeof(float),
+                                                   cudaMemcpyDeviceToHost, p.out)) != cudaSuccess))
+                return cuda_fail(ctx, e, "pipeline D2H");
+            off += f;
+        }
+        if ((e = cudaEventRecord(p.slot_free[slot], p.out)) != cudaSuccess) return cuda_fail(ctx, e, "pipeline order");
+        p.slot_used[slot] = true;
+        i = j;
+        chunk++;
+    }
+    // the caller's stream completes when the last results are on the host
+    if ((e = cudaEventRecord(p.tail, p.out)) != cudaSuccess || (e = cudaStreamWaitEvent(s, p.tail, 0)) != cudaSuccess)
+        return cuda_fail(ctx, e, "pipeline end");
+    return PC_OK;
+}
+
+pc_status pc_backproject(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* xyz) {
+    if (!ctx) return PC_ERR_INVALID_ARG;
+    pc_status st = check_image(H, W);
+    if (st != PC_OK) return st;
+    if (H == 0 || W == 0) return PC_OK;
+    if (!depth || !xyz || !aligned4(depth) || !aligned4(xyz) || !is_device_ptr(depth) || !is_device_ptr(xyz))
+        return PC_ERR_INVALID_ARG;
+    int sms = 0;
+    cudaError_t e = sm_count(ctx, &sms);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_backproject");
+    e = pcurv::launch_backproject(depth, H, W, ctx->cam, xyz, sms, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_backproject launch");
+    return PC_OK;
+}
+
+pc_status pc_initial_normals(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* normal) {
+    if (!ctx) return PC_ERR_INVALID_ARG;
+    pc_status st = check_image(H, W);
+    if (st != PC_OK) return st;
+    if (H == 0 || W == 0) return PC_OK;
+    if (!depth || !normal || !aligned4(depth) || !aligned4(normal) || !is_device_ptr(depth) ||
+        !is_device_ptr(normal))
+        return PC_ERR_INVALID_ARG;
+    const cudaError_t e = pcurv::launch_initial_normals(depth, H, W, ctx->cam, ctx->cfg.rn, ctx->cfg.det_tol,
+                                                        normal, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_initial_normals launch");
+    return PC_OK;
+}
+
 pc_status pc_destroy(pc_ctx* ctx) {
     if (!ctx) return PC_OK;
     if (ctx->stage_px) {
         cudaDeviceSynchronize();
         free_stage(ctx);
     }
+    if (ctx->pipe.device >= 0) release_pipe(ctx->pipe);
     if (ctx->batch.device >= 0) release_batch(ctx->batch);
     delete ctx;
     return PC_OK;

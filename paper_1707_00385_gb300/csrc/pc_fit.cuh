@@ -437,6 +437,49 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
     }
 }
 
+// Initial normal of Sec. 3.2.1 (Eq. initialnormal): least squares z = a x + b y + c
+// over the valid points of the (2 rn + 1)^2 patch around the pixel, in metric
+// camera coordinates centred on the pixel's own point (exact in single
+// precision: x = (du Z_i + (u0 - cx) (Z_i - Z_p)) / fx, likewise y), then
+// n = (-a, -b, 1) / sqrt(1 + a^2 + b^2).  zc, cc point at the pixel's entries
+// of staged Z and validity planes (row stride SW; valid: c == 1).  Returns
+// false when fewer than 3 points are valid or det M <= det_tol (tr M)^2.
+__device__ __forceinline__ bool initial_normal(const float* zc, const float* cc, int SW, int rn, float ap,
+                                               float bp, float Zp, const Camera& cam, float det_tol,
+                                               float& nx, float& ny, float& nz) {
+    float n = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f, sxz = 0.f, syz = 0.f;
+    for (int dv = -rn; dv <= rn; dv++) {
+        const float* zr = zc + dv * SW;
+        const float* cr = cc + dv * SW;
+        for (int du = -rn; du <= rn; du++) {
+            if (cr[du] == 1.f) {
+                const float Zi = zr[du];
+                const float dZ = Zi - Zp;
+                const float X = fmaf((float)du, Zi, ap * dZ) * cam.ifx;
+                const float Y = fmaf((float)dv, Zi, bp * dZ) * cam.ify;
+                n += 1.f;
+                sx += X; sy += Y; sz += dZ;
+                sxx = fmaf(X, X, sxx); sxy = fmaf(X, Y, sxy); syy = fmaf(Y, Y, syy);
+                sxz = fmaf(X, dZ, sxz); syz = fmaf(Y, dZ, syz);
+            }
+        }
+    }
+    // centred second moments M and v (shift by the centre point first)
+    const float in = 1.f / n;
+    const float mx = sx * in, my = sy * in, mz = sz * in;
+    const float m00 = fmaf(-sx, mx, sxx), m01 = fmaf(-sx, my, sxy), m11 = fmaf(-sy, my, syy);
+    const float w0 = fmaf(-sx, mz, sxz), w1 = fmaf(-sy, mz, syz);
+    const float det = fmaf(m00, m11, -m01 * m01), tr = m00 + m11;
+    if (n < 3.f || !(det > det_tol * tr * tr)) return false;
+    const float a = (m11 * w0 - m01 * w1) / det;
+    const float b = (m00 * w1 - m01 * w0) / det;
+    const float sc = rsqrtf(fmaf(a, a, fmaf(b, b, 1.f)));
+    nx = -a * sc;
+    ny = -b * sc;
+    nz = sc;
+    return true;
+}
+
 // The whole method for one 32 x TH output tile (tile column tx_, tile row ty_)
 // of frame f.  Called by every thread of the CTA; contains two __syncthreads
 // and leaves shared memory in use until it returns (callers that reuse smem
@@ -515,40 +558,7 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
 
     // ---- initial normal: z = a x + b y + c over the valid (2rn+1)^2 patch
     float nx = 0.f, ny = 0.f, nz = 1.f;
-    if (ok) {
-        float n = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f, sxz = 0.f,
-              syz = 0.f;
-        for (int dv = -cfg.rn; dv <= cfg.rn; dv++) {
-            const float* zr = zc + dv * SW;
-            const float* cr = cc + dv * SW;
-            for (int du = -cfg.rn; du <= cfg.rn; du++) {
-                if (cr[du] == 1.f) {
-                    const float Zi = zr[du];
-                    const float dZ = Zi - Zp;
-                    const float X = fmaf((float)du, Zi, ap * dZ) * cam.ifx;
-                    const float Y = fmaf((float)dv, Zi, bp * dZ) * cam.ify;
-                    n += 1.f;
-                    sx += X; sy += Y; sz += dZ;
-                    sxx = fmaf(X, X, sxx); sxy = fmaf(X, Y, sxy); syy = fmaf(Y, Y, syy);
-                    sxz = fmaf(X, dZ, sxz); syz = fmaf(Y, dZ, syz);
-                }
-            }
-        }
-        // centred second moments M and v (shift by the centre point first)
-        const float in = 1.f / n;
-        const float mx = sx * in, my = sy * in, mz = sz * in;
-        const float m00 = fmaf(-sx, mx, sxx), m01 = fmaf(-sx, my, sxy), m11 = fmaf(-sy, my, syy);
-        const float w0 = fmaf(-sx, mz, sxz), w1 = fmaf(-sy, mz, syz);
-        const float det = fmaf(m00, m11, -m01 * m01), tr = m00 + m11;
-        if (n < 3.f || !(det > cfg.det_tol * tr * tr)) {
-            ok = false;
-        } else {
-            const float a = (m11 * w0 - m01 * w1) / det;
-            const float b = (m00 * w1 - m01 * w0) / det;
-            const float sc = rsqrtf(fmaf(a, a, fmaf(b, b, 1.f)));
-            nx = -a * sc; ny = -b * sc; nz = sc;
-        }
-    }
+    if (ok) ok = initial_normal(zc, cc, SW, cfg.rn, ap, bp, Zp, cam, cfg.det_tol, nx, ny, nz);
 
     // ---- window count (row segments counted above)
     int cnt = 0;

@@ -109,6 +109,12 @@ const KernelOps* select_ops(const FitConfig& cfg);
 cudaError_t launch_pack(const float* depth, int H, int W, int format, unsigned short* packed,
                         float* tile_base, cudaStream_t stream);
 
+// Organised outputs (pc_outputs.cu): point cloud and initial-normal field.
+cudaError_t launch_backproject(const float* depth, int H, int W, const Camera& cam, float* xyz, int sms,
+                               cudaStream_t stream);
+cudaError_t launch_initial_normals(const float* depth, int H, int W, const Camera& cam, int rn, float det_tol,
+                                   float* normal, cudaStream_t stream);
+
 }  // namespace pcurv
 
 struct pc_ctx;

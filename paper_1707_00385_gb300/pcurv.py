@@ -18,6 +18,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "pcurv.h")
 PC_OK, PC_ERR_INVALID_ARG, PC_ERR_CUDA, PC_ERR_OOM, PC_ERR_TIMEOUT, PC_ERR_UNSUPPORTED = range(6)
 PC_MAX_RADIUS, PC_MAX_NORMAL_RADIUS, PC_MAX_ITERATIONS, PC_MAX_DIM, PC_MAX_BATCH = 24, 8, 64, 16384, 4096
 PC_STATIC_MAX_FRAMES = 256
+PC_HOST_CHUNK_PIXELS = 4 << 20
 PC_DEPTH_F16, PC_DEPTH_BF16 = 1, 2
 PC_PACK_TILE_W, PC_PACK_TILE_H = 32, 8
 
@@ -81,13 +82,17 @@ def load() -> ctypes.CDLL:
         L.pc_plan_tile_height.restype = ctypes.c_int
         L.pc_compute_packed.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                         _vp, _vp, _vp]
+        L.pc_compute_host_batch.argtypes = [_vp, ctypes.POINTER(pc_frame), ctypes.c_int, _vp]
+        L.pc_backproject.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
+        L.pc_initial_normals.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
         L.pc_destroy.argtypes = [_vp]
         L.pc_status_string.argtypes = [ctypes.c_int]
         L.pc_status_string.restype = ctypes.c_char_p
         L.pc_last_error.argtypes = [_vp]
         L.pc_last_error.restype = ctypes.c_char_p
         for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_compute_batch",
-                  "pc_compute_batch_static", "pc_pack_depth", "pc_compute_packed", "pc_autotune", "pc_destroy"):
+                  "pc_compute_batch_static", "pc_pack_depth", "pc_compute_packed", "pc_autotune", "pc_destroy",
+                  "pc_compute_host_batch", "pc_backproject", "pc_initial_normals"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -125,6 +130,19 @@ def pc_compute_batch(ctx, frames, n, stream) -> int:
 def pc_compute_batch_static(ctx, frames, n, stream) -> int:
     """The batch entry point that allocates no device memory (fixed scratch)."""
     return load().pc_compute_batch_static(ctx, frames, n, stream)
+
+
+def pc_compute_host_batch(ctx, frames, n, stream) -> int:
+    """frames: a ctypes array of pc_frame whose buffers are host addresses."""
+    return load().pc_compute_host_batch(ctx, frames, n, stream)
+
+
+def pc_backproject(ctx, depth, H, W, stream, xyz) -> int:
+    return load().pc_backproject(ctx, depth, H, W, stream, xyz)
+
+
+def pc_initial_normals(ctx, depth, H, W, stream, normal) -> int:
+    return load().pc_initial_normals(ctx, depth, H, W, stream, normal)
 
 
 def pc_pack_depth(ctx, depth, H, W, fmt, stream, packed, tile_base) -> int:
@@ -271,6 +289,43 @@ class Curvature:
         if st != PC_OK:
             raise PcError(st, "pc_compute_packed", pc_last_error(self.ctx))
         return k1, k2, normal
+
+    def host_batch(self, frames, stream=None):
+        """pc_compute_host_batch over a list of (depth, (fx, fy, cx, cy), k1, k2,
+        normal) tuples of CPU float32 tensors (pinned for the copies to overlap;
+        normal may be None).  Synchronise the stream before reading the outputs."""
+        arr = (pc_frame * max(len(frames), 1))()
+        for i, (d, intr, a, b, n) in enumerate(frames):
+            H, W = d.shape
+            arr[i] = pc_frame(d.data_ptr(), H, W, *map(float, intr), a.data_ptr(), b.data_ptr(),
+                              n.data_ptr() if n is not None else None)
+        st = pc_compute_host_batch(self.ctx, arr if frames else None, len(frames), _stream_handle(stream))
+        if st != PC_OK:
+            raise PcError(st, "pc_compute_host_batch", pc_last_error(self.ctx))
+
+    def backproject(self, depth, xyz=None, stream=None):
+        """pc_backproject: the organised point cloud (H x W x 3) of a CUDA range image."""
+        import torch
+        H, W = depth.shape
+        depth = depth.contiguous()
+        if xyz is None:
+            xyz = torch.empty((H, W, 3), dtype=torch.float32, device=depth.device)
+        st = pc_backproject(self.ctx, depth.data_ptr(), H, W, _stream_handle(stream), xyz.data_ptr())
+        if st != PC_OK:
+            raise PcError(st, "pc_backproject", pc_last_error(self.ctx))
+        return xyz
+
+    def initial_normals(self, depth, normal=None, stream=None):
+        """pc_initial_normals: the (2 normal_radius + 1)^2 regression normals (H x W x 3)."""
+        import torch
+        H, W = depth.shape
+        depth = depth.contiguous()
+        if normal is None:
+            normal = torch.empty((H, W, 3), dtype=torch.float32, device=depth.device)
+        st = pc_initial_normals(self.ctx, depth.data_ptr(), H, W, _stream_handle(stream), normal.data_ptr())
+        if st != PC_OK:
+            raise PcError(st, "pc_initial_normals", pc_last_error(self.ctx))
+        return normal
 
     def compute_host(self, depth, k1, k2, normal=None, stream=None):
         """Host-memory form (pc_compute_host): depth, k1, k2, normal are CPU

@@ -86,10 +86,41 @@ def test_batch_argument_checks_without_gpu(pc):
         pc.pc_destroy(ctx)
 
 
+def test_host_batch_and_output_argument_checks_without_gpu(pc):
+    st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5)
+    try:
+        assert pc.pc_compute_host_batch(None, None, 0, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute_host_batch(ctx, None, 0, None) == pc.PC_OK
+        assert pc.pc_compute_host_batch(ctx, None, 1, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute_host_batch(ctx, None, -1, None) == pc.PC_ERR_INVALID_ARG
+        fr = (pc.pc_frame * 2)()
+        fr[0] = pc.pc_frame(None, 0, 0, 1.0, 1.0, 0.0, 0.0, None, None, None)      # empty frames: nothing to do
+        fr[1] = pc.pc_frame(None, 5, 0, 1.0, 1.0, 0.0, 0.0, None, None, None)
+        assert pc.pc_compute_host_batch(ctx, fr, 2, None) == pc.PC_OK
+        fr[1] = pc.pc_frame(None, 4, 4, 1.0, 1.0, 0.0, 0.0, None, None, None)      # NULL host buffers
+        assert pc.pc_compute_host_batch(ctx, fr, 2, None) == pc.PC_ERR_INVALID_ARG
+        buf = (ctypes.c_float * 64)()
+        a = ctypes.addressof(buf)
+        fr[1] = pc.pc_frame(a, 4, 4, 1.0, float("nan"), 0.0, 0.0, a, a, None)      # fy not finite
+        assert pc.pc_compute_host_batch(ctx, fr, 2, None) == pc.PC_ERR_INVALID_ARG
+        fr[1] = pc.pc_frame(a, 4, 70000, 1.0, 1.0, 0.0, 0.0, a, a, None)           # W > PC_MAX_DIM
+        assert pc.pc_compute_host_batch(ctx, fr, 2, None) == pc.PC_ERR_INVALID_ARG
+        for f in (pc.pc_backproject, pc.pc_initial_normals):
+            assert f(None, None, 0, 0, None, None) == pc.PC_ERR_INVALID_ARG
+            assert f(ctx, None, 0, 0, None, None) == pc.PC_OK
+            assert f(ctx, None, 0, 9, None, None) == pc.PC_OK
+            assert f(ctx, None, 4, 4, None, None) == pc.PC_ERR_INVALID_ARG
+            assert f(ctx, None, -1, 4, None, None) == pc.PC_ERR_INVALID_ARG
+            assert f(ctx, None, 4, pc.pcurv.PC_MAX_DIM + 1, None, None) == pc.PC_ERR_INVALID_ARG
+    finally:
+        pc.pc_destroy(ctx)
+
+
 def test_limits_match_header(pc):
     text = open(HEADER).read()
     for name in ("PC_MAX_RADIUS", "PC_MAX_NORMAL_RADIUS", "PC_MAX_ITERATIONS", "PC_MAX_DIM", "PC_MAX_BATCH",
-                 "PC_STATIC_MAX_FRAMES", "PC_DEPTH_F16", "PC_DEPTH_BF16", "PC_PACK_TILE_W", "PC_PACK_TILE_H"):
+                 "PC_STATIC_MAX_FRAMES", "PC_DEPTH_F16", "PC_DEPTH_BF16", "PC_PACK_TILE_W", "PC_PACK_TILE_H",
+                 "PC_HOST_CHUNK_PIXELS"):
         val = int(re.search(rf"#define {name} (\d+)", text).group(1))
         assert getattr(pc.pcurv, name) == val
 
