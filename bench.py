@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--report", choices=["precision", "serve", "accuracy"], default=None,
+    ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs"], default=None,
                     help="instead of the benchmark line, print the error of each precision variant "
                          "against the FP64 oracle (one 640x480 frame, radii 3, 7, 11)")
     return ap.parse_args()
@@ -342,6 +342,52 @@ def accuracy_report(args):
         print(json.dumps({"sphere_100mm_vs_noise": row}), flush=True)
 
 
+BIG_SIDE = 4096   # the organised outputs' roofline case: 16.8 Mpixel, 268 MB of HBM traffic > L2
+
+
+def outputs_report(curv, depth, stream, device_time, steps):
+    """Organised outputs of the same frames: pc_backproject (HBM-bound: 4 B in,
+    12 B out per pixel) and pc_initial_normals, per 640x480 frame (one launch
+    each, launch-latency bound) and on one 4096 x 4096 image tiled from the
+    frames (the kernels' own throughput; inputs and outputs larger than L2)."""
+    import torch
+    H_, W_ = depth[0].shape
+    F_ = len(depth)
+    xyz = [torch.empty((H_, W_, 3), device=depth[0].device) for _ in range(F_)]
+    n0 = [torch.empty((H_, W_, 3), device=depth[0].device) for _ in range(F_)]
+    ms_bp = device_time(lambda: [curv.backproject(depth[i], xyz[i], stream=stream) for i in range(F_)], steps) / steps / F_
+    ms_n0 = device_time(lambda: [curv.initial_normals(depth[i], n0[i], stream=stream) for i in range(F_)],
+                        steps) / steps / F_
+    del xyz, n0
+    reps = (BIG_SIDE + H_ - 1) // H_, (BIG_SIDE + W_ - 1) // W_
+    big = torch.cat([torch.cat([depth[(i * reps[1] + j) % F_] for j in range(reps[1])], 1)
+                     for i in range(reps[0])], 0)[:BIG_SIDE, :BIG_SIDE].contiguous()
+    bxyz = torch.empty((BIG_SIDE, BIG_SIDE, 3), device=big.device)
+    bn0 = torch.empty((BIG_SIDE, BIG_SIDE, 3), device=big.device)
+    big_steps = 4 * steps
+    ms_bbp = device_time(lambda: curv.backproject(big, bxyz, stream=stream), big_steps) / big_steps
+    ms_bn0 = device_time(lambda: curv.initial_normals(big, bn0, stream=stream), big_steps) / big_steps
+    del big, bxyz, bn0
+    px = BIG_SIDE * BIG_SIDE
+    hbm_peak = measured_hbm_gbs()
+    gbs = 16 * px / (ms_bbp * 1e-3) / 1e9
+    normal_flop = px * (FLOP_PER_NORMAL_PT * 49 + 20)     # 7x7 patch, 2x2 solve and normalisation
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    return {
+        "backproject": {
+            "ms_per_640x480_frame": ms_bp, "ms_4096x4096": ms_bbp, "mpixel_per_s_4096x4096": px / ms_bbp / 1e3,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs / hbm_peak if hbm_peak else None, "algorithmic_bytes_per_pixel": 16,
+                         "case": "one 4096x4096 image", "peak_basis": "measured HBM copy bandwidth"}},
+        "initial_normals": {
+            "ms_per_640x480_frame": ms_n0, "ms_4096x4096": ms_bn0, "mpixel_per_s_4096x4096": px / ms_bn0 / 1e3,
+            "roofline": {"bound": "alu", "achieved": normal_flop / (ms_bn0 * 1e-3) / 1e12, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": normal_flop / (ms_bn0 * 1e-3) / 1e12 / alu_peak,
+                         "counted_flop_per_pixel": FLOP_PER_NORMAL_PT * 49 + 20, "case": "one 4096x4096 image"}},
+    }
+
+
 def precision_report(args):
     """Error of each precision variant against the FP64 oracle on one seeded
     640x480 Kinect-like frame, per window radius, with its time per frame."""
@@ -401,6 +447,33 @@ def main():
         return
     if args.report == "accuracy":
         accuracy_report(args)
+        return
+    if args.report == "outputs":
+        import torch
+        import paper_1707_00385_gb300 as pc
+        from paper_1707_00385_gb300 import build as pcbuild
+        pcbuild.build()
+        sc = scenes(max(1, min(args.scenes, args.frames)))
+        depth = [torch.from_numpy(sc[i % len(sc)].depth).cuda() for i in range(args.frames)]
+        curv = pc.Curvature(*sc[0].intrinsics, window_radius=RADIUS, iterations=ITERS)
+        stream = torch.cuda.Stream()
+
+        def device_time(step, steps):
+            with torch.cuda.stream(stream):
+                for _ in range(max(3, args.warmup)):
+                    step()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        print(json.dumps({"outputs": outputs_report(curv, depth, stream, device_time, max(2, args.steps // 4))}),
+              flush=True)
+        curv.close()
         return
     if args.report == "serve":
         # the serving workload: 20,000 requests at 2,000/s, then a point at half the
@@ -568,32 +641,8 @@ def main():
     e2e_pf_steps = max(1, args.steps // 4)
     e2e_pf_val = float(world) * e2e_pf_steps * F * H * W / wall_time(step_host_frames, e2e_pf_steps) / 1e6
 
-    # ---- organised outputs (point cloud, initial-normal field) over the same frames
-    xyz = [torch.empty((H, W, 3), device=dev) for _ in range(F)]
-    n0 = [torch.empty((H, W, 3), device=dev) for _ in range(F)]
-
-    def step_backproject():
-        for i in range(F):
-            curv.backproject(depth[i], xyz[i], stream=stream)
-
-    def step_normals():
-        for i in range(F):
-            curv.initial_normals(depth[i], n0[i], stream=stream)
-
-    out_steps = max(2, args.steps // 4)
-    ms_bp = device_time(step_backproject, out_steps) / out_steps / F
-    ms_n0 = device_time(step_normals, out_steps) / out_steps / F
-    hbm_peak = measured_hbm_gbs()
-    outputs = {
-        "backproject": {"ms_per_frame": ms_bp, "mpixel_per_s": H * W / ms_bp / 1e3,
-                        "roofline": {"bound": "hbm", "achieved": 16 * H * W / (ms_bp * 1e-3) / 1e9,
-                                     "peak": hbm_peak, "unit": "GB/s",
-                                     "frac": (16 * H * W / (ms_bp * 1e-3) / 1e9 / hbm_peak) if hbm_peak else None,
-                                     "algorithmic_bytes_per_pixel": 16,
-                                     "peak_basis": "measured HBM copy bandwidth (MEASURED_PEAKS.json)"}},
-        "initial_normals": {"ms_per_frame": ms_n0, "mpixel_per_s": H * W / ms_n0 / 1e3},
-    }
-    del xyz, n0
+    # ---- organised outputs (point cloud, initial-normal field)
+    outputs = outputs_report(curv, depth, stream, device_time, max(2, args.steps // 4))
 
     # ---- roofline of the persistent kernel: counted FP32 work vs the FP32 ALU peak
     props = torch.cuda.get_device_properties(dev)

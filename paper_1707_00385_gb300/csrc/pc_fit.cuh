@@ -438,41 +438,64 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
 }
 
 // Initial normal of Sec. 3.2.1 (Eq. initialnormal): least squares z = a x + b y + c
-// over the valid points of the (2 rn + 1)^2 patch around the pixel, in metric
-// camera coordinates centred on the pixel's own point (exact in single
-// precision: x = (du Z_i + (u0 - cx) (Z_i - Z_p)) / fx, likewise y), then
-// n = (-a, -b, 1) / sqrt(1 + a^2 + b^2).  zc, cc point at the pixel's entries
-// of staged Z and validity planes (row stride SW; valid: c == 1).  Returns
-// false when fewer than 3 points are valid or det M <= det_tol (tr M)^2.
-__device__ __forceinline__ bool initial_normal(const float* zc, const float* cc, int SW, int rn, float ap,
-                                               float bp, float Zp, const Camera& cam, float det_tol,
-                                               float& nx, float& ny, float& nz) {
-    float n = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f, sxz = 0.f, syz = 0.f;
-    for (int dv = -rn; dv <= rn; dv++) {
-        const float* zr = zc + dv * SW;
-        const float* cr = cc + dv * SW;
-        for (int du = -rn; du <= rn; du++) {
-            if (cr[du] == 1.f) {
-                const float Zi = zr[du];
-                const float dZ = Zi - Zp;
-                const float X = fmaf((float)du, Zi, ap * dZ) * cam.ifx;
-                const float Y = fmaf((float)dv, Zi, bp * dZ) * cam.ify;
-                n += 1.f;
-                sx += X; sy += Y; sz += dZ;
-                sxx = fmaf(X, X, sxx); sxy = fmaf(X, Y, sxy); syy = fmaf(Y, Y, syy);
-                sxz = fmaf(X, dZ, sxz); syz = fmaf(Y, dZ, syz);
-            }
+// over the valid points of the (2 rn + 1)^2 patch around the pixel, then
+// n = (-a, -b, 1) / sqrt(1 + a^2 + b^2).  The regression runs in pixel-scaled
+// camera coordinates centred on the pixel's own point, exact in single
+// precision: x' = fx x = du Z_i + (u0 - cx)(Z_i - Z_p), likewise y' = fy y,
+// z' = Z_i - Z_p, so a = fx a', b = fy b'.  Symmetric points (du, dv) and
+// (-du, -dv) share packed FP32x2 operations; the centre adds only to the
+// count.  zc points at the pixel's entry of a staged Z plane (row stride SW)
+// holding 0 where the range is not valid; the centre itself must be valid.
+// Returns false when fewer than 3 points are valid or det M <= det_tol (tr M)^2
+// (M in metric coordinates).
+__device__ __forceinline__ bool initial_normal(const float* zc, int SW, int rn, float ap, float bp, float Zp,
+                                               const Camera& cam, float det_tol, float& nx, float& ny,
+                                               float& nz) {
+    f32x2 N = 0ull, SX = 0ull, SY = 0ull, SZ = 0ull, SXX = 0ull, SXY = 0ull, SYY = 0ull, SXZ = 0ull,
+          SYZ = 0ull;
+    const f32x2 AP = splat(ap), BP = splat(bp), NZP = splat(-Zp);
+    const f32x2 STEP = pack(1.f, -1.f);
+    for (int dv = -rn; dv <= 0; dv++) {
+        const float* za = zc + dv * SW;
+        const float* zb = zc - dv * SW;
+        const f32x2 DV = pack((float)dv, -(float)dv);
+        f32x2 DU = pack(-(float)rn, (float)rn);
+        const int last = dv < 0 ? rn : -1;
+        for (int du = -rn; du <= last; du++) {
+            const float a = za[du], b = zb[-du];
+            const f32x2 Z = pack(a, b);
+            const f32x2 M = pack(a > 0.f ? 1.f : 0.f, b > 0.f ? 1.f : 0.f);
+            const f32x2 dZ = add2(Z, NZP);
+            const f32x2 X = fma2(DU, Z, mul2(AP, dZ));
+            const f32x2 Y = fma2(DV, Z, mul2(BP, dZ));
+            const f32x2 MX = mul2(M, X), MY = mul2(M, Y), MZ = mul2(M, dZ);
+            N = add2(N, M);
+            SX = add2(SX, MX);
+            SY = add2(SY, MY);
+            SZ = add2(SZ, MZ);
+            SXX = fma2(MX, X, SXX);
+            SXY = fma2(MX, Y, SXY);
+            SXZ = fma2(MX, dZ, SXZ);
+            SYY = fma2(MY, Y, SYY);
+            SYZ = fma2(MY, dZ, SYZ);
+            DU = add2(DU, STEP);
         }
     }
-    // centred second moments M and v (shift by the centre point first)
+    const float n = hsum(N) + 1.f;  // + the centre, at x' = y' = z' = 0
+    const float sx = hsum(SX), sy = hsum(SY), sz = hsum(SZ);
+    const float sxx = hsum(SXX), sxy = hsum(SXY), syy = hsum(SYY), sxz = hsum(SXZ), syz = hsum(SYZ);
+    // centred second moments M' and v' (shift by the centre point first)
     const float in = 1.f / n;
     const float mx = sx * in, my = sy * in, mz = sz * in;
     const float m00 = fmaf(-sx, mx, sxx), m01 = fmaf(-sx, my, sxy), m11 = fmaf(-sy, my, syy);
     const float w0 = fmaf(-sx, mz, sxz), w1 = fmaf(-sy, mz, syz);
-    const float det = fmaf(m00, m11, -m01 * m01), tr = m00 + m11;
+    // the singularity test in metric coordinates: M = S M' S, S = diag(1/fx, 1/fy)
+    const float ix2 = cam.ifx * cam.ifx, iy2 = cam.ify * cam.ify;
+    const float det = fmaf(m00, m11, -m01 * m01) * (ix2 * iy2), tr = fmaf(m00, ix2, m11 * iy2);
     if (n < 3.f || !(det > det_tol * tr * tr)) return false;
-    const float a = (m11 * w0 - m01 * w1) / det;
-    const float b = (m00 * w1 - m01 * w0) / det;
+    const float idet = 1.f / fmaf(m00, m11, -m01 * m01);
+    const float a = (m11 * w0 - m01 * w1) * idet * cam.fx;
+    const float b = (m00 * w1 - m01 * w0) * idet * cam.fy;
     const float sc = rsqrtf(fmaf(a, a, fmaf(b, b, 1.f)));
     nx = -a * sc;
     ny = -b * sc;
@@ -558,7 +581,7 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
 
     // ---- initial normal: z = a x + b y + c over the valid (2rn+1)^2 patch
     float nx = 0.f, ny = 0.f, nz = 1.f;
-    if (ok) ok = initial_normal(zc, cc, SW, cfg.rn, ap, bp, Zp, cam, cfg.det_tol, nx, ny, nz);
+    if (ok) ok = initial_normal(zc, SW, cfg.rn, ap, bp, Zp, cam, cfg.det_tol, nx, ny, nz);
 
     // ---- window count (row segments counted above)
     int cnt = 0;

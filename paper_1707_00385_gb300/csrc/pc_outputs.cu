@@ -29,41 +29,65 @@ __device__ __forceinline__ float3 point_of(float z, int u, int v, const Camera& 
 }
 
 constexpr int BP_THREADS = 256;
+constexpr int BP_WARPS = BP_THREADS / 32;
+constexpr int BP_BLOCKS_PER_SM = 8;  // 64 resident warps per SM: the whole grid is one wave
 
 // VEC: depth and xyz are 16-byte aligned and W is a multiple of 4, so that a
-// group of four pixels is one float4 of ranges, three float4 of points, and
-// lies in one row.
+// group of four pixels is one float4 of ranges and three float4 of points and
+// lies in one row.  A warp takes 32 consecutive groups (128 pixels): one
+// coalesced 512-byte load, then its 96 float4 of points go through shared
+// memory so that each of the three stores writes 512 contiguous bytes (lane l
+// stages float4 3l .. 3l+2: a quarter warp covers 8 disjoint 4-bank groups,
+// free of bank conflicts).  H * W < 2^31 (PC_MAX_DIM^2): 32-bit indices.
 template <bool VEC>
-__global__ void __launch_bounds__(BP_THREADS) k_backproject(const float* __restrict__ depth, int H, int W,
-                                                            Camera cam, float* __restrict__ xyz) {
-    const size_t n = (size_t)H * W;
-    const size_t groups = (n + 3) / 4;
-    for (size_t g = (size_t)blockIdx.x * BP_THREADS + threadIdx.x; g < groups; g += (size_t)gridDim.x * BP_THREADS) {
-        const size_t i0 = 4 * g;
-        if (VEC) {
-            const int v = (int)(i0 / (size_t)W), u = (int)(i0 - (size_t)v * W);
-            const float4 z = __ldg(reinterpret_cast<const float4*>(depth) + g);
-            const float3 p0 = point_of(z.x, u, v, cam), p1 = point_of(z.y, u + 1, v, cam),
-                         p2 = point_of(z.z, u + 2, v, cam), p3 = point_of(z.w, u + 3, v, cam);
-            float4* o = reinterpret_cast<float4*>(xyz) + 3 * g;
-            o[0] = make_float4(p0.x, p0.y, p0.z, p1.x);
-            o[1] = make_float4(p1.y, p1.z, p2.x, p2.y);
-            o[2] = make_float4(p2.z, p3.x, p3.y, p3.z);
-        } else {
-            for (size_t i = i0; i < i0 + 4 && i < n; i++) {
-                const int v = (int)(i / (size_t)W), u = (int)(i - (size_t)v * W);
-                const float3 p = point_of(depth[i], u, v, cam);
-                xyz[3 * i] = p.x;
-                xyz[3 * i + 1] = p.y;
-                xyz[3 * i + 2] = p.z;
+__global__ void __launch_bounds__(BP_THREADS, BP_BLOCKS_PER_SM)
+    k_backproject(const float* __restrict__ depth, int H, int W, Camera cam, float* __restrict__ xyz) {
+    const unsigned n = (unsigned)H * (unsigned)W;
+    const unsigned groups = (n + 3) / 4;
+    const unsigned uw = (unsigned)W;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (VEC) {
+        __shared__ float4 stage[BP_WARPS][96];
+        float4* st = stage[warp];
+        const unsigned nwarps = gridDim.x * BP_WARPS;
+        for (unsigned w0 = (blockIdx.x * BP_WARPS + warp) * 32; w0 < groups; w0 += nwarps * 32) {
+            const unsigned g = w0 + lane;
+            if (g < groups) {
+                const float4 z = __ldcs(reinterpret_cast<const float4*>(depth) + g);
+                const unsigned v = 4 * g / uw, u = 4 * g - v * uw;
+                const float3 p0 = point_of(z.x, (int)u, (int)v, cam), p1 = point_of(z.y, (int)u + 1, (int)v, cam),
+                             p2 = point_of(z.z, (int)u + 2, (int)v, cam), p3 = point_of(z.w, (int)u + 3, (int)v, cam);
+                st[3 * lane] = make_float4(p0.x, p0.y, p0.z, p1.x);
+                st[3 * lane + 1] = make_float4(p1.y, p1.z, p2.x, p2.y);
+                st[3 * lane + 2] = make_float4(p2.z, p3.x, p3.y, p3.z);
+            }
+            __syncwarp();
+            const unsigned live = 3 * min(32u, groups - w0);   // float4 of points this warp writes
+            float4* o = reinterpret_cast<float4*>(xyz) + 3 * (size_t)w0;
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const unsigned k = 32 * j + lane;
+                if (k < live) __stcs(o + k, st[k]);  // streaming: written once, not read back here
+            }
+            __syncwarp();
+        }
+    } else {
+        const unsigned stride = gridDim.x * BP_THREADS;
+        for (unsigned g = blockIdx.x * BP_THREADS + threadIdx.x; g < groups; g += stride) {
+            for (unsigned i = 4 * g; i < 4 * g + 4 && i < n; i++) {
+                const unsigned v = i / uw, u = i - v * uw;
+                const float3 p = point_of(depth[i], (int)u, (int)v, cam);
+                xyz[3 * (size_t)i] = p.x;
+                xyz[3 * (size_t)i + 1] = p.y;
+                xyz[3 * (size_t)i + 2] = p.z;
             }
         }
     }
 }
 
-// One CTA per 32 x TH output tile; Z and validity planes of the tile plus a
-// halo of rn staged in shared memory (validity as the full path stages it:
-// 1 valid, +inf not).
+// One CTA per 32 x TH output tile; the Z plane of the tile plus a halo of rn
+// staged in shared memory (0 where the range is not valid, as the full path
+// stages it).
 template <int TH>
 __global__ void __launch_bounds__(TILE_W * TH)
     k_initial_normals(const float* __restrict__ depth, int H, int W, Camera cam, int rn, float det_tol,
@@ -72,22 +96,17 @@ __global__ void __launch_bounds__(TILE_W * TH)
     constexpr int NT = TILE_W * TH;
     const int SW = TILE_W + 2 * rn, SH = TH + 2 * rn;
     float* tz = smem;
-    float* tcv = smem + SW * SH;
     const int ub = blockIdx.x * TILE_W, vb = blockIdx.y * TH;
     const int tid = threadIdx.y * TILE_W + threadIdx.x;
     for (int i = tid; i < SW * SH; i += NT) {
         const int sy = i / SW, sx = i - sy * SW;
         const int gv = vb - rn + sy, gu = ub - rn + sx;
-        float z = 0.f, c = __int_as_float(0x7f800000);
+        float z = 0.f;
         if (gu >= 0 && gu < W && gv >= 0 && gv < H) {
             const float d = __ldg(depth + (size_t)gv * W + gu);
-            if (range_ok(d)) {
-                z = d;
-                c = 1.f;
-            }
+            if (range_ok(d)) z = d;
         }
         tz[i] = z;
-        tcv[i] = c;
     }
     __syncthreads();
     const int u0 = ub + threadIdx.x, v0 = vb + threadIdx.y;
@@ -95,10 +114,10 @@ __global__ void __launch_bounds__(TILE_W * TH)
     const int cidx = (threadIdx.y + rn) * SW + threadIdx.x + rn;
     const float Zp = tz[cidx];
     float nx = 0.f, ny = 0.f, nz = 1.f;
-    bool ok = tcv[cidx] == 1.f;
+    bool ok = Zp > 0.f;
     if (ok)
-        ok = initial_normal(tz + cidx, tcv + cidx, SW, rn, (float)u0 - cam.cx, (float)v0 - cam.cy, Zp, cam,
-                            det_tol, nx, ny, nz);
+        ok = initial_normal(tz + cidx, SW, rn, (float)u0 - cam.cx, (float)v0 - cam.cy, Zp, cam, det_tol, nx, ny,
+                            nz);
     const size_t out = (size_t)v0 * W + u0;
     const float q = __int_as_float(0x7fffffff);
     normal[3 * out] = ok ? nx : q;
@@ -114,7 +133,7 @@ cudaError_t launch_backproject(const float* depth, int H, int W, const Camera& c
                                cudaStream_t stream) {
     const size_t groups = ((size_t)H * W + 3) / 4;
     const size_t want = (groups + BP_THREADS - 1) / BP_THREADS;
-    const size_t cap = (size_t)(sms > 0 ? sms : 152) * 8;  // 8 resident CTAs of 256 threads per SM
+    const size_t cap = (size_t)(sms > 0 ? sms : 152) * BP_BLOCKS_PER_SM;
     const int grid = (int)(want < cap ? want : cap);
     const bool vec = ((uintptr_t)depth & 15u) == 0 && ((uintptr_t)xyz & 15u) == 0 && (W & 3) == 0;
     if (vec)
@@ -125,7 +144,7 @@ cudaError_t launch_backproject(const float* depth, int H, int W, const Camera& c
 }
 
 size_t initial_normals_smem_bytes(int rn) {
-    return (size_t)(TILE_W + 2 * rn) * (NORMAL_TH + 2 * rn) * 2 * sizeof(float);
+    return (size_t)(TILE_W + 2 * rn) * (NORMAL_TH + 2 * rn) * sizeof(float);
 }
 
 cudaError_t launch_initial_normals(const float* depth, int H, int W, const Camera& cam, int rn, float det_tol,
