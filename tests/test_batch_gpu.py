@@ -138,3 +138,34 @@ def test_batched_frame_against_oracle(gpu, orc, frames):
     rep = parity.compare(k1, k2, n, ref, pivot_tol=1e-5)
     assert rep.ok() and rep.n_well_posed > 0.3 * rep.n_valid_oracle, rep.summary()
     assert rep.frac_within_tol_all > 0.9, rep.summary()
+
+
+def test_benchmark_launch_sampled_against_oracle(gpu, orc):
+    """The benchmark's own launch: 128 distinct 640 x 480 frame buffers (8
+    seeded scenes) in one persistent launch at r = 7, T = 5; pixels sampled
+    from four frames (random ones plus a whole corner tile) against the oracle."""
+    import torch
+    import bench
+    from oracle import parity
+    sc = bench.scenes(8)
+    F = 128
+    dev = [torch.from_numpy(sc[i % 8].depth).cuda() for i in range(F)]
+    outs = [(torch.empty(480, 640, device="cuda"), torch.empty(480, 640, device="cuda"),
+             torch.empty(480, 640, 3, device="cuda")) for _ in range(F)]
+    c = gpu.Curvature(*sc[0].intrinsics, window_radius=bench.RADIUS, iterations=bench.ITERS)
+    c.batch([(dev[i], sc[i % 8].intrinsics) + outs[i] for i in range(F)])
+    torch.cuda.synchronize()
+    c.close()
+    rng = np.random.default_rng(17)
+    corner = np.stack(np.meshgrid(np.arange(608, 640), np.arange(472, 480)), -1).reshape(-1, 2)
+    for f in (0, 37, 90, 127):
+        s = sc[f % 8]
+        uv = np.concatenate([np.stack([rng.integers(0, 640, 400), rng.integers(0, 480, 400)], 1), corner])
+        uv = uv.astype(np.int32)
+        k1, k2, n = (t.cpu().numpy() for t in outs[f])
+        ref = parity.reference(s.depth, orc.params(*s.intrinsics, r=bench.RADIUS, T=bench.ITERS,
+                                                   pivot_tol=1e-5), uv=uv)
+        rep = parity.compare(k1[uv[:, 1], uv[:, 0]], k2[uv[:, 1], uv[:, 0]], n[uv[:, 1], uv[:, 0]], ref,
+                             pivot_tol=1e-5)
+        print(f, rep.summary())
+        assert rep.ok() and rep.n_well_posed > 0.5 * rep.n_valid_oracle, rep.summary()
