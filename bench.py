@@ -56,7 +56,7 @@ METRIC = ("Mpixel/s of (k1,k2) at 640x480 r=7 vs FP32 roofline; "
 WORKLOAD = "640x480 Kinect-like synthetic scenes, window radius 7 (15x15), 5 IRLS iterations, FP32"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -69,9 +69,11 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs"], default=None,
-                    help="instead of the benchmark line, print the error of each precision variant "
-                         "against the FP64 oracle (one 640x480 frame, radii 3, 7, 11)")
-    return ap.parse_args()
+                    help="instead of the benchmark line: precision = error of each precision variant "
+                         "against the FP64 oracle (one 640x480 frame, radii 3, 7, 11); serve = the "
+                         "serving trace and a point at half capacity; accuracy = error against "
+                         "analytic ground truth; outputs = the organised outputs alone")
+    return ap.parse_args(argv)
 
 
 def scenes(n):
@@ -219,6 +221,37 @@ def cpu_baseline(frames_np, intr, seconds):
     return {"value": done / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} pixels ({done // W} rows of 640x480 seeded scenes), "
                       f"FP64 C oracle, {dt:.1f} s"}
+
+
+class Ranks:
+    """Host-side coordination of the replicas (one process per GPU, torchrun):
+    a barrier around each timed region and the maximum of a duration over the
+    ranks.  The method needs no data exchange; these are the only collectives.
+    `device` is where the reduction buffer lives (the rank's GPU under NCCL,
+    the CPU under gloo)."""
+
+    def __init__(self, world, device):
+        self.world, self.device = world, device
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(self, x):
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, seconds):
+    """Aggregate throughput of the replicas: every rank processed units_per_rank
+    units; the job took the slowest rank's time (weak scaling)."""
+    return float(world) * units_per_rank / seconds
 
 
 def run_reference(args, rank, world):
@@ -504,16 +537,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier = Ranks(world, dev).barrier
+    max_over_ranks = Ranks(world, dev).max_over_ranks
 
     nsc = max(1, min(args.scenes, args.frames))
     sc = scenes(nsc)
@@ -564,12 +589,11 @@ def main():
     clocks = {}
     ms = device_time(step_batch, args.steps, clocks)
     ms_step = ms / args.steps
-    px_total = float(world) * args.steps * F * H * W
-    value = px_total / (ms / 1e3) / 1e6
+    value = whole_job_rate(world, args.steps * F * H * W, ms / 1e3) / 1e6
     launch_ms = ms_step   # one persistent kernel per step
     # the same frames, one pc_compute launch per frame
     ms_pf = device_time(step_frames, max(2, args.steps // 2))
-    pf_value = float(world) * max(2, args.steps // 2) * F * H * W / (ms_pf / 1e3) / 1e6
+    pf_value = whole_job_rate(world, max(2, args.steps // 2) * F * H * W, ms_pf / 1e3) / 1e6
 
     # ---- uneven frames (four resolutions): one batch call vs plain launches
     un = uneven_scenes(2)
@@ -594,8 +618,8 @@ def main():
     ms_uf = device_time(step_un_frames, ub_steps)
     uneven = {"frames": 64, "resolutions": [f"{w}x{h}" for h, w, _ in UNEVEN_SIZES],
               "distinct_scenes": len(un), "pixels": un_px,
-              "batch_frames_per_s": float(world) * 64 * ub_steps / (ms_ub / 1e3),
-              "plain_launch_frames_per_s": float(world) * 64 * ub_steps / (ms_uf / 1e3),
+              "batch_frames_per_s": whole_job_rate(world, 64 * ub_steps, ms_ub / 1e3),
+              "plain_launch_frames_per_s": whole_job_rate(world, 64 * ub_steps, ms_uf / 1e3),
               "batch_ms": ms_ub / ub_steps, "plain_ms": ms_uf / ub_steps}
     for c_ in un_ctx:
         c_.close()
@@ -635,13 +659,13 @@ def main():
 
     e2e_steps = max(2, args.steps // 2)
     e2e_s = wall_time(step_host_batch, e2e_steps)
-    e2e_val = float(world) * e2e_steps * F * H * W / e2e_s / 1e6
+    e2e_val = whole_job_rate(world, e2e_steps * F * H * W, e2e_s) / 1e6
     # host path and batched device path give the same numbers
     step_batch()
     torch.cuda.synchronize()
     same = bool(np.array_equal(hk1[0].numpy(), k1[0].cpu().numpy(), equal_nan=True))
     e2e_pf_steps = max(1, args.steps // 4)
-    e2e_pf_val = float(world) * e2e_pf_steps * F * H * W / wall_time(step_host_frames, e2e_pf_steps) / 1e6
+    e2e_pf_val = whole_job_rate(world, e2e_pf_steps * F * H * W, wall_time(step_host_frames, e2e_pf_steps)) / 1e6
 
     # ---- organised outputs (point cloud, initial-normal field)
     outputs = outputs_report(curv, depth, stream, device_time, max(2, args.steps // 4))
