@@ -136,15 +136,20 @@ def kernel_sources_hash():
 
 def recorded_traffic(frames):
     """DRAM bytes of one persistent launch over `frames` 640x480 frames, from
-    the committed ncu summary (bytes per frame), if it was taken on the current
-    kernel sources (DRAM traffic grows with the frames a launch processes)."""
+    the committed ncu record of the full-size launch (128 frames), if it was
+    taken on the current kernel sources.  Larger launches scale in proportion
+    (their results overflow L2 the same way); smaller ones keep results in L2
+    and are not reported."""
     p = os.path.join(ROOT, "profiles", "k_fit_r7_640x480_traffic.txt")
     if not os.path.exists(p):
         return None
     kv = dict(l.strip().split("=", 1) for l in open(p) if "=" in l and not l.startswith("#"))
     if kv.get("kernel_sources_sha256_16") != kernel_sources_hash():
         return None
-    return float(kv["dram_bytes_per_frame"]) * frames
+    base = int(kv["frames_per_launch"])
+    if frames < base:
+        return None
+    return float(kv["dram_bytes_per_launch"]) * frames / base
 
 
 class Clocks:
