@@ -463,21 +463,23 @@ __device__ __forceinline__ bool initial_normal(const float* zc, int SW, int rn, 
         const int last = dv < 0 ? rn : -1;
         for (int du = -rn; du <= last; du++) {
             const float a = za[du], b = zb[-du];
-            const f32x2 Z = pack(a, b);
+            const f32x2 Z = pack(a, b);  // 0 where invalid
             const f32x2 M = pack(a > 0.f ? 1.f : 0.f, b > 0.f ? 1.f : 0.f);
-            const f32x2 dZ = add2(Z, NZP);
-            const f32x2 X = fma2(DU, Z, mul2(AP, dZ));
-            const f32x2 Y = fma2(DV, Z, mul2(BP, dZ));
-            const f32x2 MX = mul2(M, X), MY = mul2(M, Y), MZ = mul2(M, dZ);
+            // masked coordinates, exactly 0 for an invalid point (Z = 0, M = 0) and
+            // the unmasked values otherwise: M (Z - Zp), du Z + ap M (Z - Zp), ...;
+            // M^2 = M, so the products of masked coordinates are masked too
+            const f32x2 MZ = fma2(M, NZP, Z);
+            const f32x2 MX = fma2(DU, Z, mul2(AP, MZ));
+            const f32x2 MY = fma2(DV, Z, mul2(BP, MZ));
             N = add2(N, M);
             SX = add2(SX, MX);
             SY = add2(SY, MY);
             SZ = add2(SZ, MZ);
-            SXX = fma2(MX, X, SXX);
-            SXY = fma2(MX, Y, SXY);
-            SXZ = fma2(MX, dZ, SXZ);
-            SYY = fma2(MY, Y, SYY);
-            SYZ = fma2(MY, dZ, SYZ);
+            SXX = fma2(MX, MX, SXX);
+            SXY = fma2(MX, MY, SXY);
+            SXZ = fma2(MX, MZ, SXZ);
+            SYY = fma2(MY, MY, SYY);
+            SYZ = fma2(MY, MZ, SYZ);
             DU = add2(DU, STEP);
         }
     }
