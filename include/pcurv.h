@@ -209,7 +209,11 @@ pc_status pc_compute_batch_static(pc_ctx* ctx, const pc_frame* frames, int n, vo
  * must stay valid until then.  Results equal pc_compute's bit for bit.  The
  * ctx's batch scratch is used on the internal compute stream: do not run
  * pc_compute_batch on the same ctx concurrently.  Staging slots grow to the
- * largest chunk seen (24 B per pixel each). */
+ * largest chunk seen (24 B per pixel each).  Errors: argument errors are
+ * reported before anything is enqueued; a CUDA error in the middle of the
+ * call (e.g. PC_ERR_OOM growing a slot) returns at once, while chunks already
+ * enqueued still run on the internal streams -- synchronise the device before
+ * reusing the host buffers after an error. */
 #define PC_HOST_CHUNK_PIXELS 4194304  /* 4 Mi pixels */
 pc_status pc_compute_host_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream);
 
