@@ -140,3 +140,46 @@ def test_closed_form_paraboloid_on_gpu(gpu):
     assert k1[15, 15] == pytest.approx(6.0, rel=2e-3)
     assert k2[15, 15] == pytest.approx(-10.0, rel=2e-3)
     assert np.allclose(n[15, 15], [0, 0, 1], atol=1e-5)
+
+
+@pytest.fixture(scope="module")
+def small_crop(kinect640):
+    # 40 x 48: two tile rows with a ragged tail, small enough for the largest windows
+    return synth.crop(kinect640, 200, 300, 40, 48)
+
+
+def test_largest_window_radius(gpu, orc, small_crop):
+    """PC_MAX_RADIUS = 24 (49 x 49 window), 2 iterations."""
+    import paper_1707_00385_gb300 as pc
+    r = pc.pcurv.PC_MAX_RADIUS
+    check(gpu, orc, small_crop, r, 2, min_well_posed=0.0, min_within=0.6)
+
+
+def test_paper_sparse_37x37_window(gpu, orc, crop):
+    """The paper's sparsely sampled 37 x 37 patch: radius 18 sampled every 3 pixels."""
+    check(gpu, orc, crop, 18, 5, min_well_posed=0.2, min_within=0.75, stride=3)
+
+
+def test_most_iterations(gpu, orc, small_crop):
+    """PC_MAX_ITERATIONS = 64 at radius 3: the iterations settle, so most pixels are
+    fixed at single precision again."""
+    import paper_1707_00385_gb300 as pc
+    check(gpu, orc, small_crop, 3, pc.pcurv.PC_MAX_ITERATIONS, min_well_posed=0.5, min_within=0.8)
+
+
+def test_no_iterations(gpu, orc, crop):
+    """T = 0: curvatures 0, normal = the initial normal, validity from the
+    normal and the window count."""
+    from oracle import parity
+    k1, k2, n = run_gpu(gpu, crop.depth, crop.intrinsics, 7, 0)
+    p = orc.params(*crop.intrinsics, r=7, T=0, pivot_tol=PIVOT_TOL)
+    f = orc.curvature_image(crop.depth, p)
+    ref = parity.normal_reference(crop.depth, p)       # sensitivity of the normal itself
+    ok_o, ok_g = f.status == orc.OK, np.isfinite(k1)
+    assert np.array_equal(ok_g, np.isfinite(k2)) and np.array_equal(ok_g, np.isfinite(n).all(-1))
+    # validity agrees except where the singularity test of the regression is below resolution
+    assert np.all(~np.isfinite(ref.sens[ok_o != ok_g]))
+    assert np.all(k1[ok_g] == 0) and np.all(k2[ok_g] == 0)
+    wp = ok_o & ok_g & (ref.sens <= 0.25 * parity.NORMAL_TOL)
+    assert wp.sum() > 0.95 * ok_o.sum()
+    assert parity.angle(n[wp], f.normal[wp]).max() <= parity.NORMAL_TOL
