@@ -10,6 +10,10 @@
 #include "../../include/pcurv.h"
 #include "pc_internal.h"
 
+// The fused kernels stage halo rows of at most 96 columns (three warp ballots).
+static_assert(pcurv::TILE_W + 2 * PC_MAX_RADIUS <= 96 && PC_MAX_NORMAL_RADIUS <= PC_MAX_RADIUS,
+              "staged halo rows exceed the three ballots of the fused kernels");
+
 namespace {
 
 // Device scratch of pc_compute_batch: the frame table and the tile counter,

@@ -241,73 +241,74 @@ __device__ __forceinline__ float sq_residual2(const Coef2& k, float za, float zb
     return (ca == 1.f ? ea : 0.f) + (cb == 1.f ? eb : 0.f);
 }
 
-// 1/sqrt(x) and 1/x: hardware approximations in single precision (at most
-// 2 and 1 ulp: PTX rsqrt.approx, rcp.approx), correctly rounded in double.
-__device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
+// 1/x: hardware approximation in single precision (at most 1 ulp: PTX
+// rcp.approx), correctly rounded in double.  mul_rn / fma_rn: one rounding
+// each, written out so that no compiler contraction can differ between the
+// kernels that inline the solve (their results must agree bit for bit).
 __device__ __forceinline__ float inv(float x) {
     float y;
     asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 __device__ __forceinline__ double inv(double x) { return 1.0 / x; }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// Jacobi-scaled LDL^T solve of H b = g (H symmetric, upper triangle used),
-// returning delta = -b and the smallest scaled pivot.  T is float or double.
+// LDL^T solve of H b = g (H symmetric, upper triangle used), returning
+// delta = -b.  The factorisation is judged on the pivots of the Jacobi-scaled
+// matrix D H D, D = diag(H)^(-1/2), without forming it: D H D = (D L D^-1)
+// (D d D) (D L D^-1)^T, so its pivots are d_j / H_jj, and LDL^T without
+// pivoting has the same relative rounding errors on H as on D H D.
+//   ok:  every H_jj > 0 and every d_j > tol H_jj (a NaN fails)
+//   low: some d_j < low_tol H_jj or is NaN (the FP64 refactorisation test)
+// With M_jk = L_jk d_k:  d_j = H_jj - sum_k L_jk M_jk,
+// L_ij = (H_ji - sum_k L_ik M_jk) / d_j.  T is float or double.
 template <typename T>
-__device__ __forceinline__ void ldlt6(const T (&H)[6][6], const T (&g)[6], T delta[6], T& min_pivot,
-                                      bool& positive_diag) {
-    T D[6];
-    positive_diag = true;
-#pragma unroll
-    for (int i = 0; i < 6; i++) {
-        positive_diag = positive_diag && (H[i][i] > T(0));
-        D[i] = inv_sqrt(H[i][i] > T(0) ? H[i][i] : T(1));
-    }
-    T S[6][6], L[6][6], d[6];
-#pragma unroll
-    for (int i = 0; i < 6; i++)
-#pragma unroll
-        for (int j = i; j < 6; j++) S[i][j] = H[i][j] * D[i] * D[j];
-    min_pivot = T(1);
+__device__ __forceinline__ void ldlt6(const T (&H)[6][6], const T (&g)[6], T delta[6], T tol, T low_tol, bool& ok,
+                                      bool& low) {
+    T L[6][6], M[6][6], d[6], id[6];
+    bool good = true, under = false;
 #pragma unroll
     for (int j = 0; j < 6; j++) {
-        T dj = S[j][j];
 #pragma unroll
-        for (int k = 0; k < j; k++) dj -= L[j][k] * L[j][k] * d[k];
-        min_pivot = dj < min_pivot ? dj : min_pivot;
-        min_pivot = dj == dj ? min_pivot : T(-1);  // NaN counts as singular
+        for (int k = 0; k < j; k++) M[j][k] = mul_rn(L[j][k], d[k]);
+        T dj = H[j][j];
+#pragma unroll
+        for (int k = 0; k < j; k++) dj = fma_rn(-L[j][k], M[j][k], dj);
+        good = good & (H[j][j] > T(0)) & (dj > mul_rn(tol, H[j][j]));
+        under = under | !(dj >= mul_rn(low_tol, H[j][j]));
         d[j] = dj;
-        const T idj = inv(dj);
+        id[j] = inv(dj);
 #pragma unroll
         for (int i = j + 1; i < 6; i++) {
-            T s = S[j][i];
+            T s = H[j][i];
 #pragma unroll
-            for (int k = 0; k < j; k++) s -= L[i][k] * L[j][k] * d[k];
-            L[i][j] = s * idj;
+            for (int k = 0; k < j; k++) s = fma_rn(-L[i][k], M[j][k], s);
+            L[i][j] = mul_rn(s, id[j]);
         }
     }
-    T z[6], id[6];
-#pragma unroll
-    for (int i = 0; i < 6; i++) id[i] = inv(d[i]);
+    T z[6];
 #pragma unroll
     for (int i = 0; i < 6; i++) {
-        T s = D[i] * g[i];
+        T s = g[i];
 #pragma unroll
-        for (int k = 0; k < i; k++) s -= L[i][k] * z[k];
+        for (int k = 0; k < i; k++) s = fma_rn(-L[i][k], z[k], s);
         z[i] = s;
     }
 #pragma unroll
-    for (int i = 0; i < 6; i++) z[i] *= id[i];
+    for (int i = 0; i < 6; i++) z[i] = mul_rn(z[i], id[i]);
 #pragma unroll
     for (int i = 5; i >= 0; i--) {
         T s = z[i];
 #pragma unroll
-        for (int k = i + 1; k < 6; k++) s -= L[k][i] * z[k];
+        for (int k = i + 1; k < 6; k++) s = fma_rn(-L[k][i], z[k], s);
+        delta[i] = -s;
         z[i] = s;
     }
-#pragma unroll
-    for (int i = 0; i < 6; i++) delta[i] = -D[i] * z[i];
+    ok = good;
+    low = under;
 }
 
 // Folds the 26 pairs (with their compensations when KAHAN), adds the centre
@@ -343,40 +344,55 @@ __device__ __forceinline__ bool solve_update(const Moments2& m, const Moments2& 
     H[4][4] = m22; H[4][5] = 0.5f * m13;
     H[5][5] = 0.25f * m04;
     const float g[6] = {g0, g1, -ge, 0.5f * g3, g4, 0.5f * g5};
-    float mp;
-    bool pos;
-    ldlt6<float>(H, g, delta, mp, pos);
-    if (fp64_pivot > 0.f && pos && !(mp >= fp64_pivot)) {
-        double Hd[6][6], gd[6], dd[6], mpd;
+    bool ok, low;
+    ldlt6<float>(H, g, delta, pivot_tol, fp64_pivot, ok, low);
+    bool diag_pos = true;
+#pragma unroll
+    for (int i = 0; i < 6; i++) diag_pos = diag_pos & (H[i][i] > 0.f);
+    if (fp64_pivot > 0.f && diag_pos && low) {
+        double Hd[6][6], gd[6], dd[6];
 #pragma unroll
         for (int i = 0; i < 6; i++) {
             gd[i] = g[i];
 #pragma unroll
             for (int j = i; j < 6; j++) Hd[i][j] = H[i][j];
         }
-        ldlt6<double>(Hd, gd, dd, mpd, pos);
+        bool okd, lowd;
+        ldlt6<double>(Hd, gd, dd, (double)pivot_tol, 0.0, okd, lowd);
 #pragma unroll
         for (int i = 0; i < 6; i++) delta[i] = (float)dd[i];
-        return pos && mpd > (double)pivot_tol;
+        return okd;
     }
-    return pos && mp > pivot_tol;
+    return ok;
 }
 
 // R <- Rot(t0, t1, 0) R, Rot the rotation by angle |t| about t/|t|
 // (Rodrigues: I + sin(th)/th [t]x + (1 - cos th)/th^2 [t]x^2).
+// Gauss-Newton steps turn the frame by small angles, so both coefficients are
+// taken from their Maclaurin series in th^2 while th <= 1/2:
+//   sin(th)/th         = sum (-1)^n th^2n / (2n+1)!
+//   (1 - cos th)/th^2  = sum (-1)^n th^2n / (2n+2)!
+// through th^8; the first omitted terms are below 2.5e-11 there, far under
+// single-precision rounding.  Larger angles use sincosf.
 __device__ __forceinline__ void rotate_left(float R[9], float t0, float t1) {
     const float th2 = fmaf(t0, t0, t1 * t1);
-    float sa = 1.f, c1 = 0.5f;
-    if (th2 > 0.f) {
+    float sa, c1;
+    if (th2 <= 0.25f) {
+        sa = fmaf(fmaf(fmaf(fmaf(th2, 1.f / 362880.f, -1.f / 5040.f), th2, 1.f / 120.f), th2, -1.f / 6.f), th2,
+                  1.f);
+        c1 = fmaf(fmaf(fmaf(fmaf(th2, 1.f / 3628800.f, -1.f / 40320.f), th2, 1.f / 720.f), th2, -1.f / 24.f),
+                  th2, 0.5f);
+    } else {
         const float th = sqrtf(th2);
         float s, c;
         sincosf(0.5f * th, &s, &c);
         sa = 2.f * s * c / th;
         c1 = 2.f * s * s / th2;
     }
-    const float q[9] = {1.f - c1 * t1 * t1, c1 * t0 * t1,       sa * t1,
-                        c1 * t0 * t1,       1.f - c1 * t0 * t0, -sa * t0,
-                        -sa * t1,           sa * t0,            1.f - c1 * th2};
+    const float c1t0 = mul_rn(c1, t0), c1t1 = mul_rn(c1, t1), c01 = mul_rn(c1t0, t1);
+    const float q[9] = {fma_rn(-c1t1, t1, 1.f), c01,                    mul_rn(sa, t1),
+                        c01,                    fma_rn(-c1t0, t0, 1.f), -mul_rn(sa, t0),
+                        -mul_rn(sa, t1),        mul_rn(sa, t0),         fma_rn(-c1, th2, 1.f)};
     float o[9];
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -448,19 +464,24 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
 // holding 0 where the range is not valid; the centre itself must be valid.
 // Returns false when fewer than 3 points are valid or det M <= det_tol (tr M)^2
 // (M in metric coordinates).
-__device__ __forceinline__ bool initial_normal(const float* zc, int SW, int rn, float ap, float bp, float Zp,
+// RN > 0: patch radius fixed at compile time (loops unrolled); RN == 0: rn_rt.
+template <int RN>
+__device__ __forceinline__ bool initial_normal(const float* zc, int SW, int rn_rt, float ap, float bp, float Zp,
                                                const Camera& cam, float det_tol, float& nx, float& ny,
                                                float& nz) {
+    const int rn = RN > 0 ? RN : rn_rt;
     f32x2 N = 0ull, SX = 0ull, SY = 0ull, SZ = 0ull, SXX = 0ull, SXY = 0ull, SYY = 0ull, SXZ = 0ull,
           SYZ = 0ull;
     const f32x2 AP = splat(ap), BP = splat(bp), NZP = splat(-Zp);
     const f32x2 STEP = pack(1.f, -1.f);
+#pragma unroll
     for (int dv = -rn; dv <= 0; dv++) {
         const float* za = zc + dv * SW;
         const float* zb = zc - dv * SW;
         const f32x2 DV = pack((float)dv, -(float)dv);
         f32x2 DU = pack(-(float)rn, (float)rn);
         const int last = dv < 0 ? rn : -1;
+#pragma unroll
         for (int du = -rn; du <= last; du++) {
             const float a = za[du], b = zb[-du];
             const f32x2 Z = pack(a, b);  // 0 where invalid
@@ -496,8 +517,8 @@ __device__ __forceinline__ bool initial_normal(const float* zc, int SW, int rn, 
     const float det = fmaf(m00, m11, -m01 * m01) * (ix2 * iy2), tr = fmaf(m00, ix2, m11 * iy2);
     if (n < 3.f || !(det > det_tol * tr * tr)) return false;
     const float idet = 1.f / fmaf(m00, m11, -m01 * m01);
-    const float a = (m11 * w0 - m01 * w1) * idet * cam.fx;
-    const float b = (m00 * w1 - m01 * w0) * idet * cam.fy;
+    const float a = mul_rn(mul_rn(fma_rn(m11, w0, -mul_rn(m01, w1)), idet), cam.fx);
+    const float b = mul_rn(mul_rn(fma_rn(m00, w1, -mul_rn(m01, w0)), idet), cam.fy);
     const float sc = rsqrtf(fmaf(a, a, fmaf(b, b, 1.f)));
     nx = -a * sc;
     ny = -b * sc;
@@ -506,7 +527,7 @@ __device__ __forceinline__ bool initial_normal(const float* zc, int SW, int rn, 
 }
 
 // The whole method for one 32 x TH output tile (tile column tx_, tile row ty_)
-// of frame f.  Called by every thread of the CTA; contains two __syncthreads
+// of frame f.  Called by every thread of the CTA; contains one __syncthreads
 // and leaves shared memory in use until it returns (callers that reuse smem
 // synchronise first).
 // RW > 0: window radius fixed at compile time, dense window, columns unrolled.
@@ -514,7 +535,6 @@ __device__ __forceinline__ bool initial_normal(const float* zc, int SW, int rn, 
 template <int RW, bool REJECT, int PREC = 0, int TH = 8>
 __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cfg, int tx_, int ty_,
                                          float* smem) {
-    constexpr int NT = TILE_W * TH;  // threads
     constexpr bool KAHAN = (PREC & PREC_KAHAN) != 0;
     constexpr int FMT = prec_format(PREC);
     const float* __restrict__ depth = f.depth;
@@ -533,41 +553,60 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
     float* tcv = smem + SW * SH;            // c plane
     int* rcnt = (int*)(tcv + SW * SH);      // valid window points per (tile row, pixel column)
     const int ub = tx_ * TILE_W, vb = ty_ * TH;
-    const int tid = threadIdx.y * TILE_W + threadIdx.x;
 
-    // stage the tile + halo (Sec. 3.2, first item: the range image)
-    for (int i = tid; i < SW * SH; i += NT) {
-        const int sy = i / SW, sx = i - sy * SW;
-        const int gv = vb - halo + sy, gu = ub - halo + sx;
-        float z = 0.f, c = __int_as_float(0x7f800000);
-        if (gu >= 0 && gu < W && gv >= 0 && gv < H) {
-            float d;
-            if (FMT == 0) {
-                d = __ldg(depth + (size_t)gv * W + gu);
-            } else {
-                // centred 16-bit storage: range = tile base + offset
-                const unsigned short q = __ldg(f.packed + (size_t)gv * W + gu);
-                const float off = FMT == 1 ? __half2float(__ushort_as_half(q))
-                                           : __bfloat162float(__ushort_as_bfloat16(q));
-                d = __ldg(f.tile_base + (size_t)(gv / PACK_TILE_H) * ((W + TILE_W - 1) / TILE_W) + gu / TILE_W) +
-                    off;
-            }
-            if (d > 0.f && d <= FLT_MAX) {
-                z = d;
-                c = 1.f;
-            }
-        }
-        tz[i] = z;
-        tcv[i] = c;
+    // stage the tile + halo (Sec. 3.2, first item: the range image): warp w
+    // takes halo rows w, w + TH, ..., its lanes the columns in passes of 32.
+    // The validity bits of a row (ballots, SW <= 32 + 2 PC_MAX_RADIUS <= 96
+    // columns) give the valid window points of every row segment
+    // (columns -r0..r0 on the stride) by one population count per pixel column.
+    unsigned long long seg = 0;  // the segment's sampled offsets as bits 0..2 r0
+    if (s == 1) {
+        seg = (2ull << (2 * r0)) - 1ull;
+    } else {
+        for (int k = 0; k <= 2 * r0; k += s) seg |= 1ull << k;
     }
-    __syncthreads();
-    // valid points of each window row segment (columns -r0..r0 on the stride)
-    for (int i = tid; i < SH * TILE_W; i += NT) {
-        const int row = i / TILE_W, col = i - row * TILE_W;
-        const float* c = tcv + row * SW + col + halo;
-        int n = 0;
-        for (int du = -r0; du <= r0; du += s) n += c[du] == 1.f;
-        rcnt[i] = n;
+    const int lane = threadIdx.x;
+    for (int sy = threadIdx.y; sy < SH; sy += TH) {
+        const int gv = vb - halo + sy;
+        const bool row_in = gv >= 0 && gv < H;
+        unsigned long long lo = 0, hi = 0;  // validity of columns 0..63, 64..95
+#pragma unroll
+        for (int pass = 0; pass < 3; pass++) {
+            const int sx = pass * 32 + lane;
+            if (pass * 32 >= SW) break;  // uniform over the warp
+            const int gu = ub - halo + sx;
+            float z = 0.f, c = __int_as_float(0x7f800000);
+            if (sx < SW && row_in && gu >= 0 && gu < W) {
+                float d;
+                if (FMT == 0) {
+                    d = __ldg(depth + (size_t)gv * W + gu);
+                } else {
+                    // centred 16-bit storage: range = tile base + offset
+                    const unsigned short q = __ldg(f.packed + (size_t)gv * W + gu);
+                    const float off = FMT == 1 ? __half2float(__ushort_as_half(q))
+                                               : __bfloat162float(__ushort_as_bfloat16(q));
+                    d = __ldg(f.tile_base + (size_t)(gv / PACK_TILE_H) * ((W + TILE_W - 1) / TILE_W) +
+                              gu / TILE_W) +
+                        off;
+                }
+                if (d > 0.f && d <= FLT_MAX) {
+                    z = d;
+                    c = 1.f;
+                }
+            }
+            if (sx < SW) {
+                tz[sy * SW + sx] = z;
+                tcv[sy * SW + sx] = c;
+            }
+            const unsigned long long bits = __ballot_sync(0xffffffffu, c == 1.f);
+            if (pass == 0) lo = bits;
+            else if (pass == 1) lo |= bits << 32;
+            else hi = bits;
+        }
+        // bits col + halo - r0 ... col + halo + r0 of the row: start <= 31 + halo <= 55
+        const int start = lane + halo - r0;
+        const unsigned long long w = (lo >> start) | (start > 0 ? hi << (64 - start) : 0ull);
+        rcnt[sy * TILE_W + lane] = __popcll(w & seg);
     }
     __syncthreads();
 
@@ -583,7 +622,10 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
 
     // ---- initial normal: z = a x + b y + c over the valid (2rn+1)^2 patch
     float nx = 0.f, ny = 0.f, nz = 1.f;
-    if (ok) ok = initial_normal(zc, SW, cfg.rn, ap, bp, Zp, cam, cfg.det_tol, nx, ny, nz);
+    if (ok)
+        ok = cfg.rn == NORMAL_RADIUS_UNROLLED
+                 ? initial_normal<NORMAL_RADIUS_UNROLLED>(zc, SW, 0, ap, bp, Zp, cam, cfg.det_tol, nx, ny, nz)
+                 : initial_normal<0>(zc, SW, cfg.rn, ap, bp, Zp, cam, cfg.det_tol, nx, ny, nz);
 
     // ---- window count (row segments counted above)
     int cnt = 0;

@@ -36,6 +36,10 @@ inline int tile_h_of(int variant) { return variant == 1 ? 4 : 8; }
 // storage tiles of the 16-bit range format (pc_pack_depth): 32 x 8
 constexpr int PACK_TILE_H = 8;
 
+// The initial-normal patch radius compiled with unrolled loops: 3, the 7 x 7
+// patch of Sec. 3.2.1 (other radii run the same code with run-time loops).
+constexpr int NORMAL_RADIUS_UNROLLED = 3;
+
 inline int halo_of(const FitConfig& c) { return c.r > c.rn ? c.r : c.rn; }
 
 // Z and c planes of the tile + halo, and per-row valid counts.

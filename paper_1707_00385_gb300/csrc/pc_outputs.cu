@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(TILE_W * TH)
     float nx = 0.f, ny = 0.f, nz = 1.f;
     bool ok = Zp > 0.f;
     if (ok)
-        ok = initial_normal(tz + cidx, SW, rn, (float)u0 - cam.cx, (float)v0 - cam.cy, Zp, cam, det_tol, nx, ny,
+        ok = initial_normal<0>(tz + cidx, SW, rn, (float)u0 - cam.cx, (float)v0 - cam.cy, Zp, cam, det_tol, nx, ny,
                             nz);
     const size_t out = (size_t)v0 * W + u0;
     const float q = __int_as_float(0x7fffffff);
