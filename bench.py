@@ -66,7 +66,9 @@ def parse(argv=None):
     ap.add_argument("--scenes", type=int, default=SCENES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-requests", type=int, default=None,
+                    help="requests of the serving trace (default: 20000 with --report serve, "
+                         "2000 in the main run)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs"], default=None,
                     help="instead of the benchmark line: precision = error of each precision variant "
@@ -519,10 +521,11 @@ def main():
         # the serving workload: 20,000 requests at 2,000/s, then a point at half the
         # measured batched capacity
         un = uneven_scenes(2)
-        full = serve_trace(un, args.serve_requests, args.serve_rate, seed=11)
+        n = args.serve_requests if args.serve_requests is not None else 20000
+        full = serve_trace(un, n, args.serve_rate, seed=11)
         print(json.dumps({"serve": full}), flush=True)
         cap = full["continuous_batching"]["frames_per_s"]
-        half = serve_trace(un, args.serve_requests, 0.5 * cap, seed=12)
+        half = serve_trace(un, n, 0.5 * cap, seed=12)
         print(json.dumps({"serve_half_capacity": half}), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
@@ -631,7 +634,8 @@ def main():
 
     # ---- serving: Poisson arrivals of the mixed-resolution frames, continuous
     # batching vs one launch per frame (same frames, same trace)
-    serve_res = serve_trace(un, args.serve_requests, args.serve_rate, seed=11)
+    serve_res = serve_trace(un, args.serve_requests if args.serve_requests is not None else 2000,
+                            args.serve_rate, seed=11)
 
     # ---- end to end through the host-memory entry point (pinned buffers)
     hd = [torch.from_numpy(h).pin_memory() for h in host]

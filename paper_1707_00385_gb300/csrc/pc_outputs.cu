@@ -87,9 +87,10 @@ __global__ void __launch_bounds__(BP_THREADS, BP_BLOCKS_PER_SM)
 
 // One CTA per 32 x TH output tile; the Z plane of the tile plus a halo of rn
 // staged in shared memory (0 where the range is not valid, as the full path
-// stages it).
+// stages it).  Registers are bounded for four 256-thread CTAs per SM (the
+// 7x7 patch, unrolled, would otherwise take more and leave three).
 template <int TH>
-__global__ void __launch_bounds__(TILE_W * TH)
+__global__ void __launch_bounds__(TILE_W * TH, 4 * 8 / TH)
     k_initial_normals(const float* __restrict__ depth, int H, int W, Camera cam, int rn, float det_tol,
                       float* __restrict__ normal) {
     extern __shared__ float smem[];
@@ -116,8 +117,11 @@ __global__ void __launch_bounds__(TILE_W * TH)
     float nx = 0.f, ny = 0.f, nz = 1.f;
     bool ok = Zp > 0.f;
     if (ok)
-        ok = initial_normal<0>(tz + cidx, SW, rn, (float)u0 - cam.cx, (float)v0 - cam.cy, Zp, cam, det_tol, nx, ny,
-                            nz);
+        ok = rn == NORMAL_RADIUS_UNROLLED
+                 ? initial_normal<NORMAL_RADIUS_UNROLLED>(tz + cidx, SW, 0, (float)u0 - cam.cx, (float)v0 - cam.cy,
+                                                          Zp, cam, det_tol, nx, ny, nz)
+                 : initial_normal<0>(tz + cidx, SW, rn, (float)u0 - cam.cx, (float)v0 - cam.cy, Zp, cam, det_tol,
+                                     nx, ny, nz);
     const size_t out = (size_t)v0 * W + u0;
     const float q = __int_as_float(0x7fffffff);
     normal[3 * out] = ok ? nx : q;
