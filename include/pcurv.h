@@ -84,17 +84,28 @@ typedef struct pc_params {
     int min_window;      /* fewest valid window points accepted. Default 6 */
     int batch_graph;     /* 1 = pc_compute_batch replays a CUDA graph (copy of the frame table,
                             reset of the tile queue, persistent kernel) captured once per
-                            table capacity; 0 = enqueue the three steps directly. Default 1 */
+                            table capacity; 0 = enqueue the three steps directly.  A batch
+                            with fewer tiles than the persistent grid is always enqueued
+                            directly, with one CTA per tile. Default 1 */
     int kahan;           /* 1 = compensated (Kahan) summation of the window moments in FP32;
                             costs about 2.3x the time of plain sums. Default 0 */
     float fp64_solve_cond; /* > 0: when the scaled condition estimate of the re-weighted system
                             (1 / smallest scaled pivot) exceeds this value, the 6x6 system is
                             factorised again in FP64 and singularity is judged on the FP64
                             pivots. 0 = off (default) */
-    int tile_height;     /* pixel rows of the 32-column tile one CTA computes: 8 or 4; 0 = choose
-                            per image (the size's pc_autotune result when there is one, else 8
-                            when the image has at least 1.5 32x8 tiles per SM, else 4).  Results
-                            do not depend on it.  Default 0 */
+    int tile_height;     /* pixel rows of the 32-column tile one CTA computes with one thread per
+                            pixel: 8 or 4; 0 = choose per image (the size's pc_autotune result
+                            when there is one, else 8 when the image has at least 1.5 32x8
+                            tiles per SM, else 4).  Results do not depend on it.  Default 0 */
+    int lanes_per_pixel; /* threads that share one pixel's window: 2, 4 or 8 lanes of a warp
+                            split the window rows and add their moment sums by shuffles before
+                            each solve (tiles of 32 x 8/lanes pixels, 256 threads).  For images
+                            too small to fill the GPU with one thread per pixel; on large
+                            images it costs throughput.  It changes only the order of the
+                            moment sums, so results differ from one lane per pixel by single-
+                            precision rounding.  Needs tile_height = 0 and kahan = 0.  1 = one
+                            lane per pixel, even where pc_autotune found a lane group faster;
+                            0 = the size's pc_autotune result, else one lane.  Default 0 */
 } pc_params;
 
 /* Writes the defaults above into *p (no-op for NULL). */
@@ -168,8 +179,11 @@ typedef struct pc_frame {
  * page-locked buffers owned by ctx and copied into device scratch owned by ctx
  * (allocated on the first call, grown to the next power of two of n; the call
  * may wait for the batch before the previous one to finish reading its
- * buffer).  Results equal those of pc_compute frame by frame, bit for bit.
- * Successive batch calls on one ctx must use one stream, or synchronise in
+ * buffer).  The launch uses one thread per pixel, or the lane group that
+ * params.lanes_per_pixel forces (autotune plans do not apply to a batch).
+ * Results equal those of pc_compute frame by frame, bit for bit, where
+ * pc_compute uses the same lanes per pixel (always, unless a pc_autotune plan
+ * chose a lane group for that size).  Successive batch calls on one ctx must use one stream, or synchronise in
  * between, because the device scratch is shared. */
 pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream);
 
@@ -206,7 +220,7 @@ pc_status pc_compute_batch_static(pc_ctx* ctx, const pc_frame* frames, int n, vo
  * overlap the computation of the chunks beside it.  The work starts after
  * what is already enqueued on `stream`, and `stream` waits for the last copy
  * out: once it is synchronised every result is on the host.  Host buffers
- * must stay valid until then.  Results equal pc_compute's bit for bit.  The
+ * must stay valid until then.  Results equal pc_compute_batch's bit for bit.  The
  * ctx's batch scratch is used on the internal compute stream: do not run
  * pc_compute_batch on the same ctx concurrently.  Staging slots grow to the
  * largest chunk seen (24 B per pixel each).  Errors: argument errors are
@@ -239,17 +253,26 @@ pc_status pc_backproject(pc_ctx* ctx, const float* depth, int H, int W, void* st
  *   normal  device, H*W*3 floats */
 pc_status pc_initial_normals(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* normal);
 
-/* Times the tile shapes on this image (one warm-up and three timed runs of
- * each, on `stream`, which it synchronises), remembers the fastest for images
- * of this H x W in ctx (up to 16 sizes; the oldest is forgotten first) and
- * leaves the last run's results in the outputs (layouts as pc_compute).
- * Has no effect on the choice when params.tile_height is not 0. */
+/* Times the kernel variants on this image -- 32x8 and 32x4 tiles with one
+ * thread per pixel, and 2, 4 or 8 lanes per pixel (only the one-lane tiles
+ * when params.lanes_per_pixel is 1) -- with one warm-up and three timed runs
+ * of each on `stream`, which it synchronises; remembers the fastest for
+ * images of this H x W in ctx (up to 16 sizes; the oldest is forgotten
+ * first) and leaves the last run's results in the outputs (layouts as
+ * pc_compute).  pc_compute and pc_compute_host then use it for that size;
+ * pc_compute_batch does not (one lane per pixel unless params force a lane
+ * group).  Has no effect on the choice when params.tile_height or
+ * params.lanes_per_pixel > 1 fixes it. */
 pc_status pc_autotune(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* k1_out,
                       float* k2_out, float* normal_out);
 
-/* Tile height (8 or 4) pc_compute uses for an H x W image on the current
- * device; 0 for a NULL context or sizes out of range. */
+/* Tile height (8, 4, 2 or 1 pixel rows) pc_compute uses for an H x W image on
+ * the current device; 0 for a NULL context or sizes out of range. */
 int pc_plan_tile_height(pc_ctx* ctx, int H, int W);
+
+/* Lanes per pixel (1, 2, 4 or 8) pc_compute uses for an H x W image on the
+ * current device; 0 for a NULL context or sizes out of range. */
+int pc_plan_lanes_per_pixel(pc_ctx* ctx, int H, int W);
 
 /* Frees the context, its staging buffers, batch scratch and graphs
  * (synchronising the device first when it owns any).  NULL is a no-op

@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             raise RuntimeError(f"nvcc failed on {s}:\n{r.stderr}")
         return r.stderr
 
-    with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with ThreadPoolExecutor(max_workers=min(max(os.cpu_count() or 1, 1), len(srcs))) as ex:
         logs = list(ex.map(compile_one, zip(srcs, objs)))
     if verbose or ptxas_info:
         for l in logs:

@@ -32,7 +32,7 @@ struct BatchScratch {
     int graph_cap[2] = {0, 0};
     int graph_variant[2] = {-1, -1};
     cudaStream_t capture = nullptr;           // private stream used only for capture
-    int grid[pcurv::NUM_TILE_VARIANTS] = {0, 0};  // persistent CTAs per tile variant
+    int grid[pcurv::NUM_TILE_VARIANTS] = {};  // persistent CTAs per tile variant
     int next = 0;                             // staging copy of the next call
 };
 
@@ -113,6 +113,10 @@ pc_status check_params(const pc_params& p) {
     if (p.batch_graph != 0 && p.batch_graph != 1) return PC_ERR_INVALID_ARG;
     if (p.kahan != 0 && p.kahan != 1) return PC_ERR_INVALID_ARG;
     if (p.tile_height != 0 && p.tile_height != 8 && p.tile_height != 4) return PC_ERR_INVALID_ARG;
+    if (p.lanes_per_pixel != 0 && p.lanes_per_pixel != 1 && pcurv::variant_of_lanes(p.lanes_per_pixel) < 0)
+        return PC_ERR_INVALID_ARG;
+    // a lane group fixes its own tile (32 x 8/lanes) and runs the plain FP32 form
+    if (p.lanes_per_pixel > 1 && (p.tile_height != 0 || p.kahan)) return PC_ERR_INVALID_ARG;
     if (!(finite_f(p.fp64_solve_cond) && p.fp64_solve_cond >= 0.f)) return PC_ERR_INVALID_ARG;
     return PC_OK;
 }
@@ -170,15 +174,37 @@ int round_up_pow2(int n) {
 
 namespace pcurv {
 
+namespace {
+
+// Index 1..12: the dense window of that radius (unrolled); index 0: run-time
+// radius and stride.  Each entry joins the one-lane variants of its
+// translation unit with the lane-group variants, which take radius and stride
+// at run time for every window (pc_fit_lanes.cu: unrolled copies for each
+// radius would multiply the build time for frames that are small anyway).
+struct OpsTable {
+    KernelOps ops[13];
+    OpsTable() {
+        for (int i = 0; i <= 12; i++) {
+            const KernelOps* one = i == 0 ? ops_generic() : i <= 4 ? ops_r1_4(i) : i <= 8 ? ops_r5_8(i) : ops_r9_12(i);
+            const KernelOps* lanes = ops_lanes();
+            ops[i] = *one;
+            for (int v = 0; v < NUM_TILE_VARIANTS; v++) {
+                if (!lanes->fit[v]) continue;
+                ops[i].fit[v] = lanes->fit[v];
+                ops[i].batch[v] = lanes->batch[v];
+                ops[i].occupancy[v] = lanes->occupancy[v];
+            }
+        }
+    }
+};
+
+}  // namespace
+
 const KernelOps* select_ops(const FitConfig& cfg) {
     if (cfg.kahan) return ops_precision(1, 0);
-    const KernelOps* k = nullptr;
-    if (cfg.stride == 1) {
-        if (cfg.r >= 1 && cfg.r <= 4) k = ops_r1_4(cfg.r);
-        else if (cfg.r >= 5 && cfg.r <= 8) k = ops_r5_8(cfg.r);
-        else if (cfg.r >= 9 && cfg.r <= 12) k = ops_r9_12(cfg.r);
-    }
-    return k ? k : ops_generic();
+    static const OpsTable table;  // built once (thread-safe initialisation)
+    const bool dense = cfg.stride == 1 && cfg.r >= 1 && cfg.r <= 12;
+    return &table.ops[dense ? cfg.r : 0];
 }
 
 const FitConfig& ctx_config(const pc_ctx* ctx) { return ctx->cfg; }
@@ -205,21 +231,27 @@ cudaError_t sm_count(pc_ctx* ctx, int* sms) {
     return cudaSuccess;
 }
 
+// The variant params fix (a lane group, or a one-lane tile height), else -1.
 int forced_variant(const pc_ctx* ctx) {
+    if (ctx->params.lanes_per_pixel > 1) return pcurv::variant_of_lanes(ctx->params.lanes_per_pixel);
     return ctx->params.tile_height == 8 ? 0 : ctx->params.tile_height == 4 ? 1 : -1;
 }
+
+// Whether the autotuner and the plans may use variant v: lanes_per_pixel = 1
+// keeps to one lane per pixel.
+bool plan_allows(const pc_ctx* ctx, int v) { return ctx->params.lanes_per_pixel != 1 || pcurv::lanes_of(v) == 1; }
 
 // 32 x 8 tiles when there are at least 1.5 per SM, else 32 x 4 (GB300:
 // 32 x 4 is a third faster at 160 x 120, even at 320 x 240).
 int heuristic_variant(long long tiles8, int sms) { return 2 * tiles8 >= 3LL * sms ? 0 : 1; }
 
-// Tile variant for one H x W image: forced, tuned, or the heuristic; always
-// one that ops has.
+// Tile variant for one H x W image: forced, tuned, or the heuristic (one lane
+// per pixel); always one that ops has.
 cudaError_t variant_for(pc_ctx* ctx, const pcurv::KernelOps* ops, int H, int W, int* v) {
     int choice = forced_variant(ctx);
     if (choice < 0) {
         for (const Plan& pl : ctx->plans)
-            if (pl.stamp && pl.H == H && pl.W == W) choice = pl.variant;
+            if (pl.stamp && pl.H == H && pl.W == W && plan_allows(ctx, pl.variant)) choice = pl.variant;
     }
     if (choice < 0) {
         int sms = 0;
@@ -261,6 +293,7 @@ void pc_params_default(pc_params* p) {
     p->kahan = 0;
     p->fp64_solve_cond = 0.f;
     p->tile_height = 0;
+    p->lanes_per_pixel = 0;
 }
 
 pc_status pc_create(float fx, float fy, float cx, float cy, int window_radius, int iterations,
@@ -322,7 +355,7 @@ pc_status pc_autotune(pc_ctx* ctx, const float* depth, int H, int W, void* strea
     int best = 0;
     float best_ms = 3.4e38f;
     for (int v = 0; v < pcurv::NUM_TILE_VARIANTS && e == cudaSuccess; v++) {
-        if (!ops->fit[v]) continue;
+        if (!ops->fit[v] || !plan_allows(ctx, v)) continue;
         e = ops->fit[v](f, ctx->cfg, s);
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
         for (int i = 0; i < 3 && e == cudaSuccess; i++) e = ops->fit[v](f, ctx->cfg, s);
@@ -350,6 +383,16 @@ int pc_plan_tile_height(pc_ctx* ctx, int H, int W) {
         return 0;
     }
     return pcurv::tile_h_of(v);
+}
+
+int pc_plan_lanes_per_pixel(pc_ctx* ctx, int H, int W) {
+    if (!ctx || check_image(H, W) != PC_OK) return 0;
+    int v = 0;
+    if (variant_for(ctx, pcurv::select_ops(ctx->cfg), H, W, &v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return pcurv::lanes_of(v);
 }
 
 static bool aligned2(const void* p) { return ((uintptr_t)p & 1u) == 0; }
@@ -459,7 +502,7 @@ static pc_status ensure_batch(pc_ctx* ctx, int n) {
     const int cap = round_up_pow2(n < 16 ? 16 : n);
     const size_t bytes = pcurv::batch_table_bytes(cap);
     const pcurv::KernelOps* ops = pcurv::select_ops(ctx->cfg);
-    int sms = 0, bps[pcurv::NUM_TILE_VARIANTS] = {0, 0};
+    int sms = 0, bps[pcurv::NUM_TILE_VARIANTS] = {};
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return cuda_fail(ctx, e, "batch occupancy");
     for (int v = 0; v < pcurv::NUM_TILE_VARIANTS; v++)
@@ -481,13 +524,14 @@ static pc_status ensure_batch(pc_ctx* ctx, int n) {
     return PC_OK;
 }
 
-// Copy of the staged table, queue reset and persistent kernel (tile variant v), on `s`.
-static cudaError_t enqueue_batch(pc_ctx* ctx, int slot, size_t bytes, int v, cudaStream_t s) {
+// Copy of the staged table, queue reset and persistent kernel (tile variant v,
+// `grid` CTAs), on `s`.
+static cudaError_t enqueue_batch(pc_ctx* ctx, int slot, size_t bytes, int v, int grid, cudaStream_t s) {
     BatchScratch& b = ctx->batch;
     cudaError_t e = cudaMemcpyAsync(b.d_table, b.h_table[slot], bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-    return pcurv::select_ops(ctx->cfg)->batch[v](b.d_table, b.d_counter, b.grid[v], ctx->cfg, s);
+    return pcurv::select_ops(ctx->cfg)->batch[v](b.d_table, b.d_counter, grid, ctx->cfg, s);
 }
 
 // The graph of staging copy `slot` (captured on the private stream once per
@@ -502,7 +546,7 @@ static pc_status ensure_graph(pc_ctx* ctx, int slot, int v) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b.capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture begin");
-    const cudaError_t e1 = enqueue_batch(ctx, slot, pcurv::batch_table_bytes(b.cap), v, b.capture);
+    const cudaError_t e1 = enqueue_batch(ctx, slot, pcurv::batch_table_bytes(b.cap), v, b.grid[v], b.capture);
     e = cudaStreamEndCapture(b.capture, &g);
     if (e1 != cudaSuccess || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -573,10 +617,16 @@ pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* str
     t->nframes = live;
     t->total_tiles = begin;
     cudaStream_t s = (cudaStream_t)stream;
-    if (ctx->params.batch_graph) {
+    // A queue shorter than the persistent grid gets one CTA per tile: the
+    // hardware spreads a small grid over the SMs, while the first CTAs of a
+    // full persistent grid may share SMs (GB300: one 160 x 120 frame in 32 x 4
+    // tiles, 150 tiles on a 608-CTA grid, took 88 us against 58 us).  Such
+    // launches bypass the graph, which holds the full grid.
+    const int grid = begin < b.grid[v] ? begin : b.grid[v];
+    if (ctx->params.batch_graph && grid == b.grid[v]) {
         if ((st = ensure_graph(ctx, slot, v)) != PC_OK) return st;
         if ((e = cudaGraphLaunch(b.graph[slot], s)) != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
-    } else if ((e = enqueue_batch(ctx, slot, pcurv::batch_table_bytes(live), v, s)) != cudaSuccess) {
+    } else if ((e = enqueue_batch(ctx, slot, pcurv::batch_table_bytes(live), v, grid, s)) != cudaSuccess) {
         return cuda_fail(ctx, e, "batch launch");
     }
     if ((e = cudaEventRecord(b.done[slot], s)) != cudaSuccess) return cuda_fail(ctx, e, "batch event");

@@ -453,6 +453,70 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
     }
 }
 
+// The share of one lane of a group of G lanes that computes one pixel
+// together: the window splits into row units, units 0 .. r0/s - 1 being the
+// rows dv = -r0 + k s (each point paired with its reflection (-du, -dv)) and
+// the last unit the centre row (du < 0 paired with -du); lane `sub` visits
+// units sub, sub + G, ...  Every lane runs the same number of units and the
+// same columns, so the group never diverges: a unit past the last is visited
+// with every point masked, and so are the centre row's columns du >= 0
+// (masked: c = +inf, weight exactly 0).
+template <int RW, int G, typename F>
+__device__ __forceinline__ void for_each_pair_lanes(const float* zc, const float* cc, int SW, int r, int s, int sub,
+                                                    F&& f) {
+    const int r0 = (r / s) * s;
+    const int units = r0 / s + 1;
+    const int per_lane = RW > 0 ? (RW + G) / G : (units + G - 1) / G;
+    const float INF = __int_as_float(0x7f800000);
+    const f32x2 STEP = pack((float)s, -(float)s);
+#pragma unroll
+    for (int ui = 0; ui < per_lane; ui++) {
+        const int k = sub + ui * G;
+        const bool live = k < units, centre = k == units - 1;
+        const int dv = live ? -r0 + k * s : 0;
+        const float *za = zc + dv * SW, *zb = zc - dv * SW;
+        const float *ca = cc + dv * SW, *cb = cc - dv * SW;
+        const f32x2 DV = pack((float)dv, -(float)dv);
+        f32x2 DU = pack(-(float)r0, (float)r0);
+        if (RW > 0) {
+#pragma unroll
+            for (int du = -RW; du <= RW; du++) {
+                const bool off = !live || (centre && du >= 0);
+                f(za[du], zb[-du], off ? INF : ca[du], off ? INF : cb[-du], DU, DV);
+                DU = add2(DU, STEP);
+            }
+        } else {
+            for (int du = -r0; du <= r0; du += s) {
+                const bool off = !live || (centre && du >= 0);
+                f(za[du], zb[-du], off ? INF : ca[du], off ? INF : cb[-du], DU, DV);
+                DU = add2(DU, STEP);
+            }
+        }
+    }
+}
+
+// Sum of v over the G adjacent lanes of a group (butterfly).  Every lane ends
+// with the same bits: each step adds the same two numbers in every lane.
+template <int G>
+__device__ __forceinline__ float lane_group_sum(float v) {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Folds each of the 26 pairs and sums it over the lane group (the second half
+// of each pair is left 0, so the solve's own fold returns the group total).
+template <int G>
+__device__ __forceinline__ void reduce_lanes(Moments2& m) {
+#define PC_GROUP(f) m.f = pack(lane_group_sum<G>(hsum(m.f)), 0.f);
+    PC_GROUP(h00) PC_GROUP(h01) PC_GROUP(h11) PC_GROUP(s0) PC_GROUP(s1)
+    PC_GROUP(h03) PC_GROUP(h04) PC_GROUP(h05) PC_GROUP(h13) PC_GROUP(h14) PC_GROUP(h15)
+    PC_GROUP(sw) PC_GROUP(sxx) PC_GROUP(sxy) PC_GROUP(syy)
+    PC_GROUP(m40) PC_GROUP(m31) PC_GROUP(m22) PC_GROUP(m13) PC_GROUP(m04)
+    PC_GROUP(g0) PC_GROUP(g1) PC_GROUP(ge) PC_GROUP(g3) PC_GROUP(g4) PC_GROUP(g5)
+#undef PC_GROUP
+}
+
 // Initial normal of Sec. 3.2.1 (Eq. initialnormal): least squares z = a x + b y + c
 // over the valid points of the (2 rn + 1)^2 patch around the pixel, then
 // n = (-a, -b, 1) / sqrt(1 + a^2 + b^2).  The regression runs in pixel-scaled
@@ -527,16 +591,23 @@ __device__ __forceinline__ bool initial_normal(const float* zc, int SW, int rn_r
 }
 
 // The whole method for one 32 x TH output tile (tile column tx_, tile row ty_)
-// of frame f.  Called by every thread of the CTA; contains one __syncthreads
-// and leaves shared memory in use until it returns (callers that reuse smem
-// synchronise first).
+// of frame f.  Called by every thread of the CTA (32 x TH G threads, TH G
+// warps); contains one __syncthreads and leaves shared memory in use until it
+// returns (callers that reuse smem synchronise first).
 // RW > 0: window radius fixed at compile time, dense window, columns unrolled.
 // RW == 0: radius and stride from cfg.
-template <int RW, bool REJECT, int PREC = 0, int TH = 8>
+// G: lanes per pixel.  G = 1: one thread per pixel.  G > 1: G adjacent lanes
+// share a pixel's window rows (for_each_pair_lanes) and sum their moments
+// (reduce_lanes) before each solve, which every lane of the group repeats;
+// only the order of the moment sums differs from G = 1.
+template <int RW, bool REJECT, int PREC = 0, int TH = 8, int G = 1>
 __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cfg, int tx_, int ty_,
                                          float* smem) {
     constexpr bool KAHAN = (PREC & PREC_KAHAN) != 0;
     constexpr int FMT = prec_format(PREC);
+    constexpr int NW = TH * G;  // warps of the CTA
+    static_assert(G == 1 || G == 2 || G == 4 || G == 8, "lanes per pixel");
+    static_assert(G == 1 || (!KAHAN && FMT == 0), "lane groups run the plain FP32 form");
     const float* __restrict__ depth = f.depth;
     const int H = f.H, W = f.W;
     const Camera cam = f.cam;
@@ -555,7 +626,7 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
     const int ub = tx_ * TILE_W, vb = ty_ * TH;
 
     // stage the tile + halo (Sec. 3.2, first item: the range image): warp w
-    // takes halo rows w, w + TH, ..., its lanes the columns in passes of 32.
+    // takes halo rows w, w + NW, ..., its lanes the columns in passes of 32.
     // The validity bits of a row (ballots, SW <= 32 + 2 PC_MAX_RADIUS <= 96
     // columns) give the valid window points of every row segment
     // (columns -r0..r0 on the stride) by one population count per pixel column.
@@ -566,7 +637,7 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
         for (int k = 0; k <= 2 * r0; k += s) seg |= 1ull << k;
     }
     const int lane = threadIdx.x;
-    for (int sy = threadIdx.y; sy < SH; sy += TH) {
+    for (int sy = threadIdx.y; sy < SH; sy += NW) {
         const int gv = vb - halo + sy;
         const bool row_in = gv >= 0 && gv < H;
         unsigned long long lo = 0, hi = 0;  // validity of columns 0..63, 64..95
@@ -610,15 +681,31 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
     }
     __syncthreads();
 
-    const int u0 = ub + threadIdx.x, v0 = vb + threadIdx.y;
-    if (u0 >= W || v0 >= H) return;   // no barrier follows in this function
-    const size_t out = (size_t)v0 * W + u0;
-    const int cidx = (threadIdx.y + halo) * SW + threadIdx.x + halo;
+    // the thread's pixel (tile column pxl, row pyl) and its lane in the group
+    int pxl, pyl, sub = 0;
+    if constexpr (G == 1) {
+        pxl = threadIdx.x;
+        pyl = threadIdx.y;
+    } else {
+        const int t = threadIdx.y * TILE_W + threadIdx.x;
+        pxl = (t / G) % TILE_W;
+        pyl = t / G / TILE_W;
+        sub = t % G;
+    }
+    const int u0 = ub + pxl, v0 = vb + pyl;
+    const bool inside = u0 < W && v0 < H;
+    // no barrier follows in this function; lane groups keep every lane for
+    // their shuffles (a pixel outside the image computes on staged values and
+    // stores nothing)
+    if constexpr (G == 1) {
+        if (!inside) return;
+    }
+    const int cidx = (pyl + halo) * SW + pxl + halo;
     const float* zc = tz + cidx;
     const float* cc = tcv + cidx;
     const float Zp = *zc;
     const float ap = (float)u0 - cam.cx, bp = (float)v0 - cam.cy;
-    bool ok = *cc == 1.f;
+    bool ok = (G == 1 || inside) && *cc == 1.f;
 
     // ---- initial normal: z = a x + b y + c over the valid (2rn+1)^2 patch
     float nx = 0.f, ny = 0.f, nz = 1.f;
@@ -630,7 +717,7 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
     // ---- window count (row segments counted above)
     int cnt = 0;
     if (ok) {
-        const int* rc = rcnt + (threadIdx.y + halo) * TILE_W + threadIdx.x;
+        const int* rc = rcnt + (pyl + halo) * TILE_W + pxl;
         for (int dv = -r0; dv <= r0; dv += s) cnt += rc[dv * TILE_W];
         ok = cnt >= cfg.min_window;
     }
@@ -647,7 +734,12 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
 
     // sigma = 1/sqrt(k) scales the residuals carried by the loop (Coef2)
     const float sig = sqrtf(cfg.invk), isig = 1.f / sig, hscale = 2.f * isig;
-    for (int it = 0; ok && it < cfg.T; it++) {
+    for (int it = 0; it < cfg.T; it++) {
+        if constexpr (G == 1) {
+            if (!ok) break;
+        } else {
+            if (!__any_sync(0xffffffffu, ok)) break;  // uniform over the warp
+        }
         Coef2 k;
         const float cx0 = R[0] * cam.ifx, cy0 = R[1] * cam.ify;
         const float cx1 = R[3] * cam.ifx, cy1 = R[4] * cam.ify;
@@ -671,10 +763,15 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
             // MSE of the window at this iteration; keep eps^2 <= ratio * MSE
             // (both sides in units of k: e^2 = eps^2 / k)
             float se = 0.f;
-            for_each_pair<RW>(zc, cc, SW, r, s, [&](float za, float zb, float ca, float cb, f32x2 DU,
-                                                    f32x2 DV) {
+            auto sq = [&](float za, float zb, float ca, float cb, f32x2 DU, f32x2 DV) {
                 se += sq_residual2(k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1), mul2(DV, CY2));
-            });
+            };
+            if constexpr (G == 1) {
+                for_each_pair<RW>(zc, cc, SW, r, s, sq);
+            } else {
+                for_each_pair_lanes<RW, G>(zc, cc, SW, r, s, sub, sq);
+                se = lane_group_sum<G>(se);
+            }
             const float esc = -sig * tz0;
             se += esc * esc;
             thr = cfg.reject_ratio * (se / (float)cnt);
@@ -685,26 +782,35 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
         Moments2 m, comp;
         zero(m);
         zero(comp);
+        auto first = [&](float za, float zb, float ca, float cb, f32x2 DU, f32x2 DV) {
+            visit2<REJECT, KAHAN, true>(m, comp, k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1),
+                                        mul2(DV, CY2), thr);
+        };
+        auto later = [&](float za, float zb, float ca, float cb, f32x2 DU, f32x2 DV) {
+            visit2<REJECT, KAHAN, false>(m, comp, k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1),
+                                         mul2(DV, CY2), thr);
+        };
         if (it == 0) {
             // A = B = C = 0 here: the cheaper first-iteration form
-            for_each_pair<RW>(zc, cc, SW, r, s, [&](float za, float zb, float ca, float cb, f32x2 DU,
-                                                    f32x2 DV) {
-                visit2<REJECT, KAHAN, true>(m, comp, k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1),
-                                            mul2(DV, CY2), thr);
-            });
+            if constexpr (G == 1) for_each_pair<RW>(zc, cc, SW, r, s, first);
+            else for_each_pair_lanes<RW, G>(zc, cc, SW, r, s, sub, first);
             first_iteration_sums(m, comp);
         } else {
-            for_each_pair<RW>(zc, cc, SW, r, s, [&](float za, float zb, float ca, float cb, f32x2 DU,
-                                                    f32x2 DV) {
-                visit2<REJECT, KAHAN, false>(m, comp, k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1),
-                                             mul2(DV, CY2), thr);
-            });
+            if constexpr (G == 1) for_each_pair<RW>(zc, cc, SW, r, s, later);
+            else for_each_pair_lanes<RW, G>(zc, cc, SW, r, s, sub, later);
         }
+        if constexpr (G > 1) reduce_lanes<G>(m);
 
         float dl[6];
-        if (!solve_update<KAHAN>(m, comp, wcr, ec, isig, cfg.pivot_tol, cfg.fp64_pivot, dl)) {
-            ok = false;
-            break;
+        const bool solved = solve_update<KAHAN>(m, comp, wcr, ec, isig, cfg.pivot_tol, cfg.fp64_pivot, dl);
+        if constexpr (G == 1) {
+            if (!solved) {
+                ok = false;
+                break;
+            }
+        } else {
+            ok = ok && solved;  // every lane of the group decides alike
+            if (!ok) continue;
         }
         rotate_left(R, dl[0], dl[1]);
         tz0 += dl[2];
@@ -713,6 +819,10 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
         C += dl[5];
     }
 
+    if constexpr (G > 1) {
+        if (sub != 0 || !inside) return;
+    }
+    const size_t out = (size_t)v0 * W + u0;
     if (!ok) {
         k1o[out] = qnan();
         k2o[out] = qnan();
@@ -740,26 +850,27 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
 // one CTA per SM instead of spilling.
 #define PC_BLOCKS_OF(PREC) (((PREC) & PREC_KAHAN) ? 1 : PC_MIN_BLOCKS)
 
-template <int RW, bool REJECT, int PREC, int TH>
-__global__ void __launch_bounds__(TILE_W * TH, PC_BLOCKS_OF(PREC) * (8 / TH)) k_fit(FrameArgs f, FitConfig cfg) {
+template <int RW, bool REJECT, int PREC, int TH, int G>
+__global__ void __launch_bounds__(TILE_W * TH * G, PC_BLOCKS_OF(PREC) * (8 / (TH * G)))
+    k_fit(FrameArgs f, FitConfig cfg) {
     extern __shared__ float smem[];
-    fit_tile<RW, REJECT, PREC, TH>(f, cfg, blockIdx.x, blockIdx.y, smem);
+    fit_tile<RW, REJECT, PREC, TH, G>(f, cfg, blockIdx.x, blockIdx.y, smem);
 }
 
 // Persistent form over many frames: the CTAs take (frame, tile) items from a
-// flattened queue with one atomic per tile until it is empty.  The header and
-// descriptors live in device memory (BatchTable); *next_tile must be 0 at launch.
-template <int RW, bool REJECT, int PREC, int TH>
-__global__ void __launch_bounds__(TILE_W * TH, PC_BLOCKS_OF(PREC) * (8 / TH))
+// flattened queue until it is empty.  CTA b first takes item b -- the first
+// CTAs of a launch are spread over the SMs, so a queue shorter than the grid
+// still gets one item per SM -- then items gridDim.x, gridDim.x + 1, ... with
+// one atomic each.  The header and descriptors live in device memory
+// (BatchTable); *next_tile must be 0 at launch.
+template <int RW, bool REJECT, int PREC, int TH, int G>
+__global__ void __launch_bounds__(TILE_W * TH * G, PC_BLOCKS_OF(PREC) * (8 / (TH * G)))
     k_fit_batch(const BatchTable* __restrict__ table, unsigned* __restrict__ next_tile, FitConfig cfg) {
     extern __shared__ float smem[];
     __shared__ int s_tile;
     const int nframes = table->nframes, total = table->total_tiles;
     const BatchFrame* __restrict__ fr = table->frames;
-    for (;;) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) s_tile = (int)atomicAdd(next_tile, 1u);
-        __syncthreads();
-        const int t = s_tile;
+    for (int t = blockIdx.x;;) {
         if (t >= total) break;  // uniform over the CTA
         // last frame whose first tile is <= t
         int lo = 0, hi = nframes - 1;
@@ -769,50 +880,66 @@ __global__ void __launch_bounds__(TILE_W * TH, PC_BLOCKS_OF(PREC) * (8 / TH))
         }
         const int local = t - fr[lo].tile_begin, tiles_x = fr[lo].tiles_x;
         const int ty_ = local / tiles_x;
-        fit_tile<RW, REJECT, PREC, TH>(fr[lo].f, cfg, local - ty_ * tiles_x, ty_, smem);
+        fit_tile<RW, REJECT, PREC, TH, G>(fr[lo].f, cfg, local - ty_ * tiles_x, ty_, smem);
         __syncthreads();  // shared memory and s_tile are reused by the next tile
+        if (threadIdx.x == 0 && threadIdx.y == 0) s_tile = (int)(gridDim.x + atomicAdd(next_tile, 1u));
+        __syncthreads();
+        t = s_tile;
     }
 }
 
-template <int RW, int PREC, int TH>
+template <int RW, int PREC, int TH, int G = 1>
 cudaError_t launch_fit_rw(const FrameArgs& f, const FitConfig& cfg, cudaStream_t stream) {
-    const dim3 block(TILE_W, TH);
+    const dim3 block(TILE_W, TH * G);
     const dim3 grid((f.W + TILE_W - 1) / TILE_W, (f.H + TH - 1) / TH);
     const size_t smem = fit_smem_bytes(cfg, TH);
     if (cfg.reject)
-        k_fit<RW, true, PREC, TH><<<grid, block, smem, stream>>>(f, cfg);
+        k_fit<RW, true, PREC, TH, G><<<grid, block, smem, stream>>>(f, cfg);
     else
-        k_fit<RW, false, PREC, TH><<<grid, block, smem, stream>>>(f, cfg);
+        k_fit<RW, false, PREC, TH, G><<<grid, block, smem, stream>>>(f, cfg);
     return cudaGetLastError();
 }
 
-template <int RW, int PREC, int TH>
+template <int RW, int PREC, int TH, int G = 1>
 cudaError_t launch_batch_rw(const BatchTable* table, unsigned* next_tile, int grid, const FitConfig& cfg,
                             cudaStream_t stream) {
-    const dim3 block(TILE_W, TH);
+    const dim3 block(TILE_W, TH * G);
     const size_t smem = fit_smem_bytes(cfg, TH);
     if (cfg.reject)
-        k_fit_batch<RW, true, PREC, TH><<<grid, block, smem, stream>>>(table, next_tile, cfg);
+        k_fit_batch<RW, true, PREC, TH, G><<<grid, block, smem, stream>>>(table, next_tile, cfg);
     else
-        k_fit_batch<RW, false, PREC, TH><<<grid, block, smem, stream>>>(table, next_tile, cfg);
+        k_fit_batch<RW, false, PREC, TH, G><<<grid, block, smem, stream>>>(table, next_tile, cfg);
     return cudaGetLastError();
 }
 
-template <int RW, int PREC, int TH>
+template <int RW, int PREC, int TH, int G = 1>
 cudaError_t occupancy_rw(const FitConfig& cfg, int* blocks_per_sm) {
     const size_t smem = fit_smem_bytes(cfg, TH);
     return cfg.reject ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            blocks_per_sm, k_fit_batch<RW, true, PREC, TH>, TILE_W * TH, smem)
+                            blocks_per_sm, k_fit_batch<RW, true, PREC, TH, G>, TILE_W * TH * G, smem)
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            blocks_per_sm, k_fit_batch<RW, false, PREC, TH>, TILE_W * TH, smem);
+                            blocks_per_sm, k_fit_batch<RW, false, PREC, TH, G>, TILE_W * TH * G, smem);
 }
 
-// The op table of radius RW (RW = 0: run-time radius) for both tile variants.
+// The one-lane variants (32 x 8 and 32 x 4 tiles) of radius RW (RW = 0:
+// run-time radius); the lane-group entries stay empty.
 template <int RW, int PREC>
 const KernelOps* make_ops() {
     static const KernelOps k = {{launch_fit_rw<RW, PREC, 8>, launch_fit_rw<RW, PREC, 4>},
                                 {launch_batch_rw<RW, PREC, 8>, launch_batch_rw<RW, PREC, 4>},
                                 {occupancy_rw<RW, PREC, 8>, occupancy_rw<RW, PREC, 4>}};
+    return &k;
+}
+
+// The lane-group variants of radius RW (FP32 ranges, plain sums): 32 x 4
+// pixels with 2 lanes each, 32 x 2 with 4, 32 x 1 with 8 (256 threads each);
+// the one-lane entries stay empty.
+template <int RW>
+const KernelOps* make_lane_ops() {
+    static const KernelOps k = {
+        {nullptr, nullptr, launch_fit_rw<RW, 0, 4, 2>, launch_fit_rw<RW, 0, 2, 4>, launch_fit_rw<RW, 0, 1, 8>},
+        {nullptr, nullptr, launch_batch_rw<RW, 0, 4, 2>, launch_batch_rw<RW, 0, 2, 4>, launch_batch_rw<RW, 0, 1, 8>},
+        {nullptr, nullptr, occupancy_rw<RW, 0, 4, 2>, occupancy_rw<RW, 0, 2, 4>, occupancy_rw<RW, 0, 1, 8>}};
     return &k;
 }
 

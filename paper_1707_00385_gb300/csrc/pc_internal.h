@@ -27,12 +27,25 @@ struct FitConfig {
     float fp64_pivot;  // refactorise in FP64 below this scaled pivot (0 = never)
 };
 
-// Output tile of one CTA: TILE_W x th pixels, one thread per pixel, in two
-// variants (th = 8: 256 threads; th = 4: 128 threads, for frames with few
-// tiles).  The per-pixel arithmetic does not depend on the variant.
+// Output tile of one CTA: TILE_W x th pixels, in five variants
+//   0: 32 x 8 pixels, one thread each (256 threads)
+//   1: 32 x 4 pixels, one thread each (128 threads; frames with few tiles)
+//   2: 32 x 4 pixels, 2 lanes each; 3: 32 x 2, 4 lanes; 4: 32 x 1, 8 lanes
+//      (256 threads; the lanes of a pixel share its window rows)
+// Variants 0 and 1 give the same bits; the lane groups add the moment sums in
+// another order, which changes single-precision rounding only.
 constexpr int TILE_W = 32;
-constexpr int NUM_TILE_VARIANTS = 2;
-inline int tile_h_of(int variant) { return variant == 1 ? 4 : 8; }
+constexpr int NUM_TILE_VARIANTS = 5;
+inline int tile_h_of(int variant) {
+    constexpr int h[NUM_TILE_VARIANTS] = {8, 4, 4, 2, 1};
+    return h[variant];
+}
+inline int lanes_of(int variant) {
+    constexpr int g[NUM_TILE_VARIANTS] = {1, 1, 2, 4, 8};
+    return g[variant];
+}
+// The variant of a lane-group size (2, 4, 8), else -1.
+inline int variant_of_lanes(int lanes) { return lanes == 2 ? 2 : lanes == 4 ? 3 : lanes == 8 ? 4 : -1; }
 // storage tiles of the 16-bit range format (pc_pack_depth): 32 x 8
 constexpr int PACK_TILE_H = 8;
 
@@ -95,18 +108,21 @@ struct KernelOps {
 };
 
 // Instantiation groups (one translation unit each, compiled in parallel);
-// each returns its table for radius r, or nullptr.
+// each returns its table for radius r, or nullptr.  ops_r* and ops_generic
+// hold the one-lane variants, ops_lanes the lane-group variants (run-time
+// radius and stride, serving every window).
 const KernelOps* ops_r1_4(int r);
 const KernelOps* ops_r5_8(int r);
 const KernelOps* ops_r9_12(int r);
 const KernelOps* ops_generic();
+const KernelOps* ops_lanes();
 
 // Run-time-radius kernels of the precision variants: compensated sums and/or
 // 16-bit range storage (format 0 float32, 1 FP16, 2 BF16).
 const KernelOps* ops_precision(int kahan, int format);
 
 // The instantiation serving cfg (dense radii 1..12 unrolled, anything else
-// run-time; compensated sums on the precision kernels).
+// run-time; compensated sums on the precision kernels), all five variants.
 const KernelOps* select_ops(const FitConfig& cfg);
 
 // Packs float32 ranges into per-tile-centred 16-bit storage (format 1 FP16, 2 BF16).

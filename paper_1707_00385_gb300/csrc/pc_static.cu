@@ -128,7 +128,8 @@ extern "C" pc_status pc_compute_batch_static(pc_ctx* ctx, const pc_frame* frames
         return fail(ctx, PC_ERR_CUDA, "frame table copy", e);
     if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s)) != cudaSuccess)
         return fail(ctx, PC_ERR_CUDA, "counter reset", e);
-    if ((e = ops->batch[0](table, counter, sms * (bps > 0 ? bps : 1), cfg, s)) != cudaSuccess)
+    const int slots = sms * (bps > 0 ? bps : 1);  // one CTA per tile when the queue is shorter
+    if ((e = ops->batch[0](table, counter, begin < slots ? begin : slots, cfg, s)) != cudaSuccess)
         return fail(ctx, PC_ERR_CUDA, "launch", e);
     return PC_OK;
 }

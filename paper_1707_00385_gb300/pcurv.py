@@ -37,6 +37,7 @@ class pc_params(ctypes.Structure):
         ("kahan", ctypes.c_int),
         ("fp64_solve_cond", ctypes.c_float),
         ("tile_height", ctypes.c_int),
+        ("lanes_per_pixel", ctypes.c_int),
     ]
 
 
@@ -80,6 +81,8 @@ def load() -> ctypes.CDLL:
         L.pc_autotune.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.pc_plan_tile_height.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
         L.pc_plan_tile_height.restype = ctypes.c_int
+        L.pc_plan_lanes_per_pixel.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+        L.pc_plan_lanes_per_pixel.restype = ctypes.c_int
         L.pc_compute_packed.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                         _vp, _vp, _vp]
         L.pc_compute_host_batch.argtypes = [_vp, ctypes.POINTER(pc_frame), ctypes.c_int, _vp]
@@ -161,6 +164,10 @@ def pc_plan_tile_height(ctx, H, W) -> int:
     return load().pc_plan_tile_height(ctx, H, W)
 
 
+def pc_plan_lanes_per_pixel(ctx, H, W) -> int:
+    return load().pc_plan_lanes_per_pixel(ctx, H, W)
+
+
 def pc_destroy(ctx) -> int:
     return load().pc_destroy(ctx)
 
@@ -237,8 +244,9 @@ class Curvature:
         return k1, k2, normal
 
     def autotune(self, depth, stream=None):
-        """pc_autotune on this image: times the tile shapes, remembers the
-        fastest for its size; returns the tile height now planned."""
+        """pc_autotune on this image: times the kernel variants (tile shapes,
+        lanes per pixel), remembers the fastest for its size; returns the tile
+        height now planned (lanes_per_pixel(H, W) gives the lanes)."""
         import torch
         H, W = depth.shape
         k1 = torch.empty((H, W), device=depth.device)
@@ -252,6 +260,9 @@ class Curvature:
 
     def tile_height(self, H, W):
         return pc_plan_tile_height(self.ctx, H, W)
+
+    def lanes_per_pixel(self, H, W):
+        return pc_plan_lanes_per_pixel(self.ctx, H, W)
 
     def batch(self, frames, stream=None):
         """pc_compute_batch over a list of (depth, (fx, fy, cx, cy), k1, k2, normal)

@@ -131,6 +131,7 @@ def test_defaults(pc):
     assert p.normal_radius == 3 and p.stride == 1 and p.min_window == 6
     assert p.pivot_tol == pytest.approx(1e-5) and p.det_tol == pytest.approx(1e-6)
     assert p.batch_graph == 1 and p.kahan == 0 and p.fp64_solve_cond == 0.0 and p.tile_height == 0
+    assert p.lanes_per_pixel == 0
 
 
 def test_status_strings(pc):
@@ -155,12 +156,40 @@ def test_create_rejects_bad_arguments(pc, args):
                                          ("normal_radius", 9), ("stride", 0), ("min_window", 5),
                                          ("pivot_tol", -1.0), ("det_tol", float("inf")),
                                          ("batch_graph", 2), ("kahan", 3), ("fp64_solve_cond", -1.0),
-                                         ("tile_height", 5), ("tile_height", 16)])
+                                         ("tile_height", 5), ("tile_height", 16),
+                                         ("lanes_per_pixel", 3), ("lanes_per_pixel", 16),
+                                         ("lanes_per_pixel", -1)])
 def test_create_rejects_bad_params(pc, field, value):
     p = pc.pc_params_default()
     setattr(p, field, value)
     st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5, p)
     assert st == pc.PC_ERR_INVALID_ARG and ctx is None
+
+
+@pytest.mark.parametrize("fields", [{"lanes_per_pixel": 2, "tile_height": 8},
+                                    {"lanes_per_pixel": 4, "tile_height": 4},
+                                    {"lanes_per_pixel": 8, "kahan": 1}])
+def test_create_rejects_lane_groups_with_a_fixed_tile_or_compensated_sums(pc, fields):
+    p = pc.pc_params_default()
+    for k, v in fields.items():
+        setattr(p, k, v)
+    st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5, p)
+    assert st == pc.PC_ERR_INVALID_ARG and ctx is None
+
+
+@pytest.mark.parametrize("lanes,tile", [(2, 4), (4, 2), (8, 1)])
+def test_forced_lane_group_plans(pc, lanes, tile):
+    p = pc.pc_params_default()
+    p.lanes_per_pixel = lanes
+    st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5, p)
+    assert st == pc.PC_OK
+    try:
+        for H, W in ((480, 640), (5, 7)):
+            assert pc.pc_plan_lanes_per_pixel(ctx, H, W) == lanes    # forced: no GPU query needed
+            assert pc.pc_plan_tile_height(ctx, H, W) == tile
+    finally:
+        pc.pc_destroy(ctx)
+    assert pc.pc_plan_lanes_per_pixel(None, 10, 10) == 0
 
 
 def test_compute_argument_checks_without_gpu(pc):

@@ -1,0 +1,149 @@
+"""Lane groups: 2, 4 or 8 lanes of a warp share one pixel's window rows and
+add their moment sums by shuffles before each solve.  Only the order of the
+sums differs from one thread per pixel, so the lane groups are held to the
+same rule against the FP64 oracle (oracle/parity.py); a batch with a forced
+lane group equals pc_compute with it bit for bit; pixels outside the image
+store nothing; the autotuner picks among all variants."""
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+PIVOT_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_00385_gb300 import build
+    build.build()
+    import paper_1707_00385_gb300 as pc
+    pc.load()
+    return pc
+
+
+@pytest.fixture(scope="module")
+def scenes():
+    k = synth.kinect_scene(0)
+    return {"sphere": synth.sphere_scene(0),
+            "crop": synth.crop(k, 180, 250, 70, 100),        # several tiles, ragged in both directions
+            "small": synth.crop(k, 200, 300, 37, 45)}
+
+
+# (scene, r, T, params, well-posed floor, all-pixel floor): the one-lane cases' floors
+CASES = {
+    "sphere_r3_T3": ("sphere", 3, 3, {}, 0.85, 0.9),
+    "crop_r7": ("crop", 7, 5, {}, 0.5, 0.8),
+    "crop_r11": ("crop", 11, 5, {}, 0.3, 0.8),
+    "crop_stride2": ("crop", 7, 5, {"stride": 2}, 0.5, 0.8),
+    "crop_reject": ("crop", 7, 5, {"reject": 1}, 0.5, 0.8),
+}
+_refs = {}
+
+
+def run(pc, depth, intr, r, T, **params):
+    import torch
+    c = pc.Curvature(*intr, window_radius=r, iterations=T, **params)
+    k1, k2, n = c(torch.from_numpy(np.ascontiguousarray(depth, dtype=np.float32)).cuda())
+    torch.cuda.synchronize()
+    out = k1.cpu().numpy(), k2.cpu().numpy(), n.cpu().numpy()
+    c.close()
+    return out
+
+
+def reference(orc, name, scene, r, T, params):
+    from oracle import parity
+    if name not in _refs:
+        okw = {("rn" if k == "normal_radius" else k): v for k, v in params.items()}
+        p = orc.params(*scene.intrinsics, r=r, T=T, pivot_tol=PIVOT_TOL, **okw)
+        _refs[name] = parity.reference(scene.depth, p, nthreads=0)
+    return _refs[name]
+
+
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+@pytest.mark.parametrize("case", list(CASES))
+def test_lane_group_against_oracle(gpu, orc, scenes, case, lanes):
+    from oracle import parity
+    sname, r, T, params, min_wp, min_within = CASES[case]
+    s = scenes[sname]
+    k1, k2, n = run(gpu, s.depth, s.intrinsics, r, T, lanes_per_pixel=lanes, **params)
+    rep = parity.compare(k1, k2, n, reference(orc, case, s, r, T, params), pivot_tol=PIVOT_TOL)
+    print(case, lanes, rep.summary())
+    assert rep.nan_pattern_ok
+    assert rep.n_validity_mismatch == 0, rep.summary()
+    assert rep.n_well_posed_bad == 0, rep.summary()
+    assert rep.n_well_posed >= min_wp * rep.n_valid_oracle, rep.summary()
+    assert rep.frac_within_tol_all >= min_within, rep.summary()
+    assert rep.max_normal_angle_well_posed < 1e-4, rep.summary()
+
+
+@pytest.mark.parametrize("lanes", [2, 8])
+def test_batch_with_forced_lane_group_equals_per_frame(gpu, scenes, lanes):
+    import torch
+    frames = [scenes["small"], synth.kinect_scene(5, H=120, W=160), synth.crop(scenes["crop"], 0, 0, 8, 32)]
+    ref = [run(gpu, s.depth, s.intrinsics, 7, 5, lanes_per_pixel=lanes) for s in frames]
+    c = gpu.Curvature(1.0, 1.0, 0.0, 0.0, window_radius=7, iterations=5, lanes_per_pixel=lanes)
+    args = []
+    for s in frames:
+        d = torch.from_numpy(s.depth).cuda()
+        args.append((d, s.intrinsics, torch.full(d.shape, 5.0, device="cuda"),
+                     torch.full(d.shape, 5.0, device="cuda"), torch.full(d.shape + (3,), 5.0, device="cuda")))
+    c.batch(args)
+    torch.cuda.synchronize()
+    c.close()
+    for (a1, a2, an), (_, _, b1, b2, bn) in zip(ref, args):
+        for x, y in ((a1, b1), (a2, b2), (an, bn)):
+            assert np.array_equal(x, y.cpu().numpy(), equal_nan=True)
+
+
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+def test_pixels_outside_the_image_store_nothing(gpu, scenes, lanes):
+    """37 x 45: ragged tiles in both directions; guard words after every output stay untouched."""
+    import torch
+    s = scenes["small"]
+    H, W = s.depth.shape
+    p = gpu.pc_params_default()
+    p.lanes_per_pixel = lanes
+    st, ctx = gpu.pc_create(*map(float, s.intrinsics), 7, 5, p)
+    assert st == gpu.PC_OK
+    try:
+        d = torch.from_numpy(s.depth).cuda()
+        k1 = torch.full((H * W + 256,), 7.0, device="cuda")
+        k2 = torch.full((H * W + 256,), 7.0, device="cuda")
+        n = torch.full((3 * H * W + 256,), 7.0, device="cuda")
+        assert gpu.pc_compute(ctx, d.data_ptr(), H, W, None, k1.data_ptr(), k2.data_ptr(), n.data_ptr()) == gpu.PC_OK
+        torch.cuda.synchronize()
+        assert bool((k1[H * W:] == 7.0).all()) and bool((k2[H * W:] == 7.0).all())
+        assert bool((n[3 * H * W:] == 7.0).all())
+        assert not bool((k1[:H * W] == 7.0).any())
+    finally:
+        gpu.pc_destroy(ctx)
+
+
+def test_autotune_chooses_among_all_variants(gpu, orc, scenes):
+    """On a small image any variant may win; the plan reports it, pc_compute then
+    uses it and still meets the rule; lanes_per_pixel = 1 keeps one lane."""
+    import torch
+    from oracle import parity
+    s = scenes["sphere"]
+    d = torch.from_numpy(s.depth).cuda()
+    c = gpu.Curvature(*s.intrinsics, window_radius=3, iterations=3)
+    th = c.autotune(d)
+    lanes = c.lanes_per_pixel(*s.depth.shape)
+    assert (lanes, th) in ((1, 8), (1, 4), (2, 4), (4, 2), (8, 1))
+    k1, k2, n = c(d)
+    torch.cuda.synchronize()
+    c.close()
+    rep = parity.compare(k1.cpu().numpy(), k2.cpu().numpy(), n.cpu().numpy(),
+                         reference(orc, "sphere_r3_T3", s, 3, 3, {}), pivot_tol=PIVOT_TOL)
+    assert rep.ok() and rep.n_well_posed >= 0.85 * rep.n_valid_oracle, rep.summary()
+    print("autotuned 64x48: lanes", lanes, "tile height", th)
+    one = gpu.Curvature(*s.intrinsics, window_radius=3, iterations=3, lanes_per_pixel=1)
+    one.autotune(d)
+    assert one.lanes_per_pixel(*s.depth.shape) == 1 and one.tile_height(*s.depth.shape) in (8, 4)
+    one.close()

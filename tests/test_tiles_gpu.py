@@ -1,5 +1,6 @@
-"""Tile shapes (32x8 and 32x4 pixels per CTA) and the autotuner: the shape is
-a performance choice only, results are the same bits."""
+"""Tile shapes (32x8 and 32x4 pixels per CTA, one thread per pixel) and the
+autotuner: the shape is a performance choice only, results are the same bits
+(lane groups, which the autotuner may also choose: tests/test_lanes_gpu.py)."""
 import numpy as np
 import pytest
 
@@ -64,10 +65,13 @@ def test_plan_heuristic_and_autotune(gpu):
     c = gpu.Curvature(*s.intrinsics, window_radius=7, iterations=5)
     assert c.tile_height(480, 640) == 8      # 1200 tiles of 32x8: plenty per SM
     assert c.tile_height(60, 80) == 4        # 24 tiles: too few
+    assert c.lanes_per_pixel(60, 80) == 1    # the heuristic keeps one lane per pixel
     small = synth.crop(s, 0, 0, 60, 80)
+    # the autotuner may also pick a lane group (32 x 8/lanes tiles)
+    variants = ((1, 8), (1, 4), (2, 4), (4, 2), (8, 1))
     th = c.autotune(torch.from_numpy(small.depth).cuda())
-    assert th in (4, 8) and c.tile_height(60, 80) == th
+    assert (c.lanes_per_pixel(60, 80), th) in variants and c.tile_height(60, 80) == th
     th2 = c.autotune(torch.from_numpy(s.depth).cuda())
-    assert th2 in (4, 8) and c.tile_height(480, 640) == th2
-    print("autotuned: 60x80 ->", th, "640x480 ->", th2)
+    assert (c.lanes_per_pixel(480, 640), th2) in variants and c.tile_height(480, 640) == th2
+    print("autotuned: 60x80 ->", th, c.lanes_per_pixel(60, 80), "640x480 ->", th2, c.lanes_per_pixel(480, 640))
     c.close()
