@@ -127,10 +127,12 @@ def measured_hbm_gbs():
 
 
 def kernel_sources_hash():
+    """hash of the files that define the fused kernels (device code and the
+    structures it reads); host-only files do not change the kernel"""
     d = os.path.join(ROOT, "paper_1707_00385_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if (f.startswith("pc_fit") and f.endswith((".cu", ".cuh"))) or f in ("pc_f32x2.cuh", "pc_internal.h"):
             h.update(f.encode())
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]

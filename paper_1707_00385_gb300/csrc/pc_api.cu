@@ -7,12 +7,27 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pcurv.h"
 #include "pc_internal.h"
 
 // The fused kernels stage halo rows of at most 96 columns (three warp ballots).
 static_assert(pcurv::TILE_W + 2 * PC_MAX_RADIUS <= 96 && PC_MAX_NORMAL_RADIUS <= PC_MAX_RADIUS,
               "staged halo rows exceed the three ballots of the fused kernels");
+
+namespace {
+
+// Host-side NVTX range over one API call, named after it (ncu --nvtx can
+// select kernels by it; without a CUDA tool attached the calls do nothing).
+struct HostRange {
+    explicit HostRange(const char* name) { nvtxRangePushA(name); }
+    ~HostRange() { nvtxRangePop(); }
+    HostRange(const HostRange&) = delete;
+    HostRange& operator=(const HostRange&) = delete;
+};
+
+}  // namespace
 
 namespace {
 
@@ -321,6 +336,7 @@ pc_status pc_create(float fx, float fy, float cx, float cy, int window_radius, i
 
 pc_status pc_compute(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* k1_out,
                      float* k2_out, float* normal_out) {
+    const HostRange range("pc_compute");
     if (!ctx) return PC_ERR_INVALID_ARG;
     pc_status st = check_image(H, W);
     if (st != PC_OK) return st;
@@ -338,6 +354,7 @@ pc_status pc_compute(pc_ctx* ctx, const float* depth, int H, int W, void* stream
 
 pc_status pc_autotune(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* k1_out,
                       float* k2_out, float* normal_out) {
+    const HostRange range("pc_autotune");
     if (!ctx) return PC_ERR_INVALID_ARG;
     pc_status st = check_image(H, W);
     if (st != PC_OK) return st;
@@ -414,6 +431,7 @@ pc_status pc_pack_depth(pc_ctx* ctx, const float* depth, int H, int W, int forma
 
 pc_status pc_compute_packed(pc_ctx* ctx, const unsigned short* packed, const float* tile_base, int format,
                             int H, int W, void* stream, float* k1_out, float* k2_out, float* normal_out) {
+    const HostRange range("pc_compute_packed");
     if (!ctx || (format != PC_DEPTH_F16 && format != PC_DEPTH_BF16)) return PC_ERR_INVALID_ARG;
     pc_status st = check_image(H, W);
     if (st != PC_OK) return st;
@@ -442,6 +460,7 @@ static void free_stage(pc_ctx* ctx) {
 
 pc_status pc_compute_host(pc_ctx* ctx, const float* depth_host, int H, int W, void* stream,
                           float* k1_host, float* k2_host, float* normal_host) {
+    const HostRange range("pc_compute_host");
     if (!ctx) return PC_ERR_INVALID_ARG;
     pc_status st = check_image(H, W);
     if (st != PC_OK) return st;
@@ -565,6 +584,7 @@ static pc_status ensure_graph(pc_ctx* ctx, int slot, int v) {
 }
 
 pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream) {
+    const HostRange range("pc_compute_batch");
     if (!ctx || n < 0 || n > PC_MAX_BATCH || (n > 0 && !frames)) return PC_ERR_INVALID_ARG;
     long long total = 0;  // 32 x 8 tiles
     int live = 0;
@@ -687,6 +707,7 @@ static pc_status ensure_pipe(pc_ctx* ctx) {
 }
 
 pc_status pc_compute_host_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream) {
+    const HostRange range("pc_compute_host_batch");
     if (!ctx || n < 0 || (n > 0 && !frames)) return PC_ERR_INVALID_ARG;
     size_t total_px = 0;
     for (int i = 0; i < n; i++) {
@@ -784,6 +805,7 @@ pc_status pc_compute_host_batch(pc_ctx* ctx, const pc_frame* frames, int n, void
 }
 
 pc_status pc_backproject(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* xyz) {
+    const HostRange range("pc_backproject");
     if (!ctx) return PC_ERR_INVALID_ARG;
     pc_status st = check_image(H, W);
     if (st != PC_OK) return st;
@@ -799,6 +821,7 @@ pc_status pc_backproject(pc_ctx* ctx, const float* depth, int H, int W, void* st
 }
 
 pc_status pc_initial_normals(pc_ctx* ctx, const float* depth, int H, int W, void* stream, float* normal) {
+    const HostRange range("pc_initial_normals");
     if (!ctx) return PC_ERR_INVALID_ARG;
     pc_status st = check_image(H, W);
     if (st != PC_OK) return st;

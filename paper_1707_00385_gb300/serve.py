@@ -13,6 +13,14 @@ while batches run wait only for the next free stream, so their work overlaps
 with the batches in flight.  A batch's memory returns to the budget when its
 completion event has fired.
 
+Failures stay with the requests that caused them.  A request larger than the
+whole budget is refused on arrival.  When a batch cannot be launched (an
+argument the library rejects, a host copy that fails), its requests go back to
+the head of the queue to be launched one per batch, so that one bad frame does
+not fail its neighbours; a request that fails alone is marked failed with the
+error.  When a launched batch reports an error on completion, its requests are
+marked failed.  Either way its slot and memory return, and serving goes on.
+
 Executors do the device work: GpuExecutor (batched), PlainExecutor (one
 pc_compute launch per frame on one stream, the unbatched baseline).  Clock,
 sleep and executor are parameters, so the scheduling logic runs on the CPU in
@@ -41,6 +49,8 @@ class Request:
     k1: object = None             # host results, filled when done (when the executor keeps them)
     k2: object = None
     normal: object = None
+    error: str = None             # why the request was refused or failed (None: served)
+    solo: bool = False            # retried alone after its batch failed to launch
 
     @property
     def pixels(self) -> int:
@@ -65,7 +75,7 @@ class _Batch:
 
 @dataclass
 class ServeStats:
-    requests: int
+    requests: int                 # requests served (the rates and latencies are over these)
     seconds: float                # first arrival to last completion
     frames_per_s: float
     mpixel_per_s: float
@@ -75,6 +85,8 @@ class ServeStats:
     batches: int
     peak_device_bytes: int
     budget_bytes: int
+    refused: int = 0              # larger than the whole budget
+    failed: int = 0               # launch or completion failed
     latencies_ms: list = field(default_factory=list, repr=False)
 
     def as_dict(self):
@@ -100,9 +112,6 @@ class Server:
 
     def run(self, requests, clock=time.perf_counter, sleep=time.sleep) -> ServeStats:
         reqs = sorted(requests, key=lambda r: r.t_arrival)
-        for r in reqs:
-            if r.device_bytes > self.budget:
-                raise ValueError(f"request {r.rid} needs {r.device_bytes} B, more than the budget {self.budget} B")
         n = len(reqs)
         waiting = collections.deque()
         running = []                     # batches on the GPU
@@ -111,18 +120,36 @@ class Server:
         nb = nframes = 0
         i = 0
         t0 = clock()
+
+        def fail(batch, err, t):
+            for r in batch:
+                r.error = f"{type(err).__name__}: {err}"
+                r.t_done = t
+
         while i < n or waiting or running:
             now = clock() - t0
             while i < n and reqs[i].t_arrival <= now:
-                waiting.append(reqs[i])
+                r = reqs[i]
                 i += 1
+                if r.device_bytes > self.budget:
+                    r.error = f"refused: needs {r.device_bytes} B, more than the budget of {self.budget} B"
+                    r.t_admit = r.t_done = now
+                else:
+                    waiting.append(r)
             progressed = False
             for b in list(running):
-                if self.ex.done(b.handle):
+                try:
+                    finished = self.ex.done(b.handle)
+                    if finished:
+                        self.ex.finish(b.handle, b.reqs)
+                except Exception as e:   # an error reported by the device work of this batch
+                    finished = True
+                    fail(b.reqs, e, clock() - t0)
+                if finished:
                     t = clock() - t0
-                    self.ex.finish(b.handle, b.reqs)
                     for r in b.reqs:
-                        r.t_done = t
+                        if r.error is None:
+                            r.t_done = t
                     used -= b.nbytes
                     running.remove(b)
                     free_slots.append(b.slot)
@@ -131,7 +158,7 @@ class Server:
                 batch, nbytes, px = [], 0, 0
                 while waiting and len(batch) < self.max_frames:
                     r = waiting[0]
-                    if batch and px + r.pixels > self.max_pixels:
+                    if batch and (px + r.pixels > self.max_pixels or r.solo):
                         break
                     if used + nbytes + r.device_bytes > self.budget:
                         break
@@ -139,12 +166,25 @@ class Server:
                     batch.append(r)
                     nbytes += r.device_bytes
                     px += r.pixels
+                    if r.solo:
+                        break
                 if batch:
                     slot = free_slots.pop(0)
                     t = clock() - t0
                     for r in batch:
                         r.t_admit = t
-                    handle = self.ex.launch(batch, slot)
+                    try:
+                        handle = self.ex.launch(batch, slot)
+                    except Exception as e:   # nothing of this batch is left running
+                        free_slots.append(slot)
+                        if len(batch) > 1:
+                            for r in reversed(batch):
+                                r.solo = True
+                                waiting.appendleft(r)
+                        else:
+                            fail(batch, e, clock() - t0)
+                        progressed = True
+                        continue
                     running.append(_Batch(batch, nbytes, handle, slot))
                     used += nbytes
                     peak = max(peak, used)
@@ -153,17 +193,23 @@ class Server:
                     progressed = True
             if not progressed:
                 if running:
-                    self.ex.wait(running[0].handle, self.poll_s)
+                    try:
+                        self.ex.wait(running[0].handle, self.poll_s)
+                    except Exception:
+                        pass                 # the error comes back from done() on the next pass
                 else:
                     wait = reqs[i].t_arrival - (clock() - t0) if i < n else 0.0
                     sleep(max(0.0, min(wait, 1e-3)))
-        t_end = max((r.t_done for r in reqs), default=0.0)
-        t_start = reqs[0].t_arrival if reqs else 0.0
-        lat = np.array([r.latency * 1e3 for r in reqs]) if reqs else np.zeros(1)
+        served = [r for r in reqs if r.error is None]
+        refused = sum(1 for r in reqs if r.error is not None and r.error.startswith("refused"))
+        t_end = max((r.t_done for r in served), default=0.0)
+        t_start = served[0].t_arrival if served else 0.0
+        lat = np.array([r.latency * 1e3 for r in served]) if served else np.zeros(1)
         secs = max(t_end - t_start, 1e-12)
-        return ServeStats(n, secs, n / secs, sum(r.pixels for r in reqs) / secs / 1e6,
+        return ServeStats(len(served), secs, len(served) / secs, sum(r.pixels for r in served) / secs / 1e6,
                           float(np.percentile(lat, 50)), float(np.percentile(lat, 99)),
-                          nframes / max(nb, 1), nb, peak, self.budget, list(lat))
+                          nframes / max(nb, 1), nb, peak, self.budget, refused,
+                          n - len(served) - refused, list(lat))
 
 
 class GpuExecutor:
@@ -186,10 +232,25 @@ class GpuExecutor:
         return pool.pop() if pool else self.torch.empty(shape, dtype=self.torch.float32).pin_memory()
 
     def launch(self, reqs, slot):
+        try:
+            return self._launch(reqs, slot)
+        except Exception:
+            # copies of this batch may be in flight: let them end before the
+            # buffers they use are released, and take back its host buffers
+            for st in self.streams:
+                st.synchronize()
+            for r in reqs:
+                for t in (r.k1, r.k2, r.normal):
+                    if t is not None:
+                        self._host[tuple(t.shape)].append(t)
+                r.k1 = r.k2 = r.normal = None
+            raise
+
+    def _launch(self, reqs, slot):
         torch = self.torch
         s = self.streams[slot]
-        frames, keep = [], []
-        with torch.cuda.stream(s):
+        frames = []
+        with torch.cuda.stream(s), torch.cuda.nvtx.range(f"serve batch of {len(reqs)} frames"):
             for r in reqs:
                 H, W = r.depth.shape
                 d = torch.empty((H, W), dtype=torch.float32, device="cuda")
@@ -238,7 +299,7 @@ class PlainExecutor(GpuExecutor):
         self._curv = {}
         self._args = (window_radius, iterations, params)
 
-    def launch(self, reqs, slot):
+    def _launch(self, reqs, slot):
         torch = self.torch
         s = self.streams[0]
         held = []

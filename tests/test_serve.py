@@ -1,7 +1,8 @@
 """The serving dispatcher on the CPU: a deterministic arrival trace, a fake
 clock and a fake executor that runs batches one after another at a fixed
 pixel rate.  Checks continuous batching, admission by the memory budget,
-batch limits, order and the latency bookkeeping."""
+batch limits, order, the latency bookkeeping, and failures injected on the
+host (refused frames, launches that raise, batches that report an error)."""
 import numpy as np
 import pytest
 
@@ -105,10 +106,88 @@ def test_memory_budget_bounds_admission():
     one = 1280 * 720 * BYTES_PER_PIXEL
     stats, ex = serve(reqs, budget_bytes=3 * one)
     assert stats.peak_device_bytes <= 3 * one
-    assert stats.requests == 200
-    # a frame larger than the whole budget is refused up front
-    with pytest.raises(ValueError):
-        serve(trace(3, 10), budget_bytes=one // 2)
+    assert stats.requests == 200 and stats.refused == 0 and stats.failed == 0
+
+
+def test_frames_larger_than_the_budget_are_refused_alone():
+    reqs = trace(60, 500, seed=2)
+    budget = 640 * 480 * BYTES_PER_PIXEL      # 1280 x 720 frames cannot fit
+    big = [r for r in reqs if r.pixels > 640 * 480]
+    assert big
+    stats, ex = serve(reqs, budget_bytes=budget)
+    for r in reqs:
+        if r in big:
+            assert r.error.startswith("refused") and r.t_done == r.t_admit
+        else:
+            assert r.error is None and r.t_arrival <= r.t_admit <= r.t_done
+    assert stats.refused == len(big) and stats.requests == len(reqs) - len(big) and stats.failed == 0
+    launched = {rid for _, rids, _, _ in ex.launches for rid in rids}
+    assert not launched & {r.rid for r in big}
+
+
+class FailingExecutor(FakeExecutor):
+    """Launching a batch that holds a bad request raises (as the library does
+    for an argument it rejects); a batch holding a request listed in
+    `fail_done` reports an error when it completes."""
+
+    def __init__(self, clock, bad=(), fail_done=(), **kw):
+        super().__init__(clock, **kw)
+        self.bad, self.fail_done = set(bad), set(fail_done)
+        self.attempts = []
+
+    def launch(self, batch, slot):
+        self.attempts.append([r.rid for r in batch])
+        if any(r.rid in self.bad for r in batch):
+            raise RuntimeError("pc_compute_batch: PC_ERR_INVALID_ARG (1)")
+        end = super().launch(batch, slot)
+        return (end, [r.rid for r in batch])
+
+    def done(self, h):
+        end, rids = h
+        if self.clock.t >= end and any(rid in self.fail_done for rid in rids):
+            raise RuntimeError("device work failed")
+        return super().done(end)
+
+    def wait(self, h, timeout):
+        super().wait(h[0], timeout)
+
+
+def serve_failing(reqs, **kw):
+    clk = FakeClock()
+    ex = FailingExecutor(clk, bad=kw.pop("bad", ()), fail_done=kw.pop("fail_done", ()))
+    stats = Server(ex, **kw).run(reqs, clock=clk, sleep=clk.sleep)
+    return stats, ex
+
+
+def test_a_bad_request_fails_alone_and_serving_goes_on():
+    reqs = trace(300, 3000, seed=5)          # loaded: the bad requests share batches with others
+    bad = {17, 150, 151}
+    stats, ex = serve_failing(reqs, budget_bytes=1 << 33, bad=bad)
+    for r in reqs:
+        if r.rid in bad:
+            assert "PC_ERR_INVALID_ARG" in r.error and r.t_done >= r.t_admit
+        else:
+            assert r.error is None and r.t_done is not None
+    assert stats.failed == len(bad) and stats.requests == len(reqs) - len(bad)
+    # the batches that held a bad request were retried one request per batch
+    retried = [a for a in ex.attempts if len(a) == 1 and any(b in a for b in bad)]
+    assert len(retried) == len(bad)
+    served = [rid for _, rids, _, _ in ex.launches for rid in rids]
+    assert sorted(served) == sorted(r.rid for r in reqs if r.rid not in bad)
+
+
+def test_completion_errors_fail_their_batch_and_return_its_memory():
+    reqs = trace(200, 3000, seed=6)
+    one = 1280 * 720 * BYTES_PER_PIXEL
+    stats, ex = serve_failing(reqs, budget_bytes=4 * one, fail_done={40})
+    hit = next(rids for _, rids, _, _ in ex.launches if 40 in rids)
+    for r in reqs:
+        if r.rid in hit:
+            assert r.error == "RuntimeError: device work failed"
+        else:
+            assert r.error is None
+    assert stats.failed == len(hit) and stats.requests == len(reqs) - len(hit)
+    assert stats.peak_device_bytes <= 4 * one   # the failed batch's memory came back
 
 
 def test_pixel_limit_per_batch():

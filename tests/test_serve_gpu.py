@@ -1,7 +1,8 @@
 """The serving loop on the GPU: frames of four resolutions arriving faster
 than they are served are batched continuously; every result is the same as
 the frame computed alone (bit for bit, hence within any tolerance), with the
-batched executor and with the one-launch-per-frame baseline."""
+batched executor and with the one-launch-per-frame baseline; a request the
+library rejects fails alone while the others are served."""
 import numpy as np
 import pytest
 
@@ -70,6 +71,36 @@ def test_results_same_alone_and_in_the_mix(gpu, pool, plain):
         if key not in ref:
             ref[key] = alone(gpu, r)
         a1, a2, an = ref[key]
+        assert np.array_equal(r.k1.numpy(), a1, equal_nan=True)
+        assert np.array_equal(r.k2.numpy(), a2, equal_nan=True)
+        assert np.array_equal(r.normal.numpy(), an, equal_nan=True)
+    ex.close()
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_a_rejected_request_fails_alone(gpu, pool, plain):
+    """Request 7 carries intrinsics the library rejects (fx = 0): its batch
+    fails to launch, its requests are retried one per batch, request 7 fails
+    with the library's status and every other result equals the frame alone."""
+    from paper_1707_00385_gb300.serve import GpuExecutor, PlainExecutor, Request, Server
+    reqs = make_trace(pool, 24, 4000.0, seed=8)
+    bad = reqs[7]
+    reqs[7] = Request(bad.rid, bad.depth, (0.0,) + tuple(bad.intrinsics[1:]), bad.t_arrival)
+    if plain:
+        ex = PlainExecutor(keep_results=True)
+        srv = Server(ex, budget_bytes=1 << 31, max_batch_frames=1, inflight=64)
+    else:
+        ex = GpuExecutor(keep_results=True)
+        srv = Server(ex, budget_bytes=1 << 31, max_batch_frames=16)
+    stats = srv.run(reqs)
+    print(stats.as_dict())
+    assert reqs[7].error is not None and "invalid argument (1)" in reqs[7].error, reqs[7].error
+    assert stats.failed == 1 and stats.refused == 0 and stats.requests == 23
+    for r in reqs:
+        if r is reqs[7]:
+            continue
+        assert r.error is None
+        a1, a2, an = alone(gpu, r)
         assert np.array_equal(r.k1.numpy(), a1, equal_nan=True)
         assert np.array_equal(r.k2.numpy(), a2, equal_nan=True)
         assert np.array_equal(r.normal.numpy(), an, equal_nan=True)
