@@ -274,6 +274,23 @@ int pc_plan_tile_height(pc_ctx* ctx, int H, int W);
  * current device; 0 for a NULL context or sizes out of range. */
 int pc_plan_lanes_per_pixel(pc_ctx* ctx, int H, int W);
 
+/* The plans of ctx -- per image size, the variant pc_autotune found fastest
+ * (or pc_plans_import gave) -- to keep them across processes: plans are a
+ * property of the GPU model and of the window radius, stride, iterations and
+ * precision of ctx, not of the frames.  Writes up to `capacity` plans, oldest
+ * first, into H, W, tile_height (8, 4, 2 or 1) and lanes_per_pixel (1, 2, 4
+ * or 8), and returns how many plans ctx holds (at most 16; capacity 0 with
+ * NULL arrays asks for the count); -1 for a NULL ctx or bad arrays. */
+int pc_plans_export(const pc_ctx* ctx, int* H, int* W, int* tile_height, int* lanes_per_pixel, int capacity);
+
+/* Adds n plans (0 <= n <= 64) to ctx as pc_autotune would remember them, in
+ * order (with more than 16 sizes the oldest are forgotten first).  An entry
+ * with a size out of range or empty, or a (tile_height, lanes_per_pixel) pair
+ * that is not a variant of this context, is PC_ERR_INVALID_ARG and nothing is
+ * added.  Host only: touches no GPU. */
+pc_status pc_plans_import(pc_ctx* ctx, const int* H, const int* W, const int* tile_height,
+                          const int* lanes_per_pixel, int n);
+
 /* Frees the context, its staging buffers, batch scratch and graphs
  * (synchronising the device first when it owns any).  NULL is a no-op
  * returning PC_OK. */

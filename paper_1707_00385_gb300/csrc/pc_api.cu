@@ -402,6 +402,46 @@ int pc_plan_tile_height(pc_ctx* ctx, int H, int W) {
     return pcurv::tile_h_of(v);
 }
 
+int pc_plans_export(const pc_ctx* ctx, int* H, int* W, int* tile_height, int* lanes_per_pixel, int capacity) {
+    if (!ctx || capacity < 0 || (capacity > 0 && (!H || !W || !tile_height || !lanes_per_pixel))) return -1;
+    // oldest first, so that importing them in order keeps their age order
+    const Plan* order[16];
+    int n = 0;
+    for (const Plan& pl : ctx->plans)
+        if (pl.stamp) order[n++] = &pl;
+    for (int i = 1; i < n; i++)
+        for (int j = i; j > 0 && order[j]->stamp < order[j - 1]->stamp; j--) {
+            const Plan* t = order[j];
+            order[j] = order[j - 1];
+            order[j - 1] = t;
+        }
+    for (int i = 0; i < n && i < capacity; i++) {
+        H[i] = order[i]->H;
+        W[i] = order[i]->W;
+        tile_height[i] = pcurv::tile_h_of(order[i]->variant);
+        lanes_per_pixel[i] = pcurv::lanes_of(order[i]->variant);
+    }
+    return n;
+}
+
+pc_status pc_plans_import(pc_ctx* ctx, const int* H, const int* W, const int* tile_height,
+                          const int* lanes_per_pixel, int n) {
+    const HostRange range("pc_plans_import");
+    if (!ctx || n < 0 || (n > 0 && (!H || !W || !tile_height || !lanes_per_pixel))) return PC_ERR_INVALID_ARG;
+    int v[64];
+    if (n > 64) return PC_ERR_INVALID_ARG;
+    for (int i = 0; i < n; i++) {
+        if (check_image(H[i], W[i]) != PC_OK || H[i] == 0 || W[i] == 0) return PC_ERR_INVALID_ARG;
+        v[i] = -1;
+        for (int k = 0; k < pcurv::NUM_TILE_VARIANTS; k++)
+            if (pcurv::tile_h_of(k) == tile_height[i] && pcurv::lanes_of(k) == lanes_per_pixel[i]) v[i] = k;
+        // a variant this context's kernels lack (lane groups with compensated sums) is not a plan for it
+        if (v[i] < 0 || !pcurv::select_ops(ctx->cfg)->fit[v[i]]) return PC_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n; i++) remember_plan(ctx, H[i], W[i], v[i]);
+    return PC_OK;
+}
+
 int pc_plan_lanes_per_pixel(pc_ctx* ctx, int H, int W) {
     if (!ctx || check_image(H, W) != PC_OK) return 0;
     int v = 0;

@@ -83,6 +83,11 @@ def load() -> ctypes.CDLL:
         L.pc_plan_tile_height.restype = ctypes.c_int
         L.pc_plan_lanes_per_pixel.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
         L.pc_plan_lanes_per_pixel.restype = ctypes.c_int
+        _ip = ctypes.POINTER(ctypes.c_int)
+        L.pc_plans_export.argtypes = [_vp, _ip, _ip, _ip, _ip, ctypes.c_int]
+        L.pc_plans_export.restype = ctypes.c_int
+        L.pc_plans_import.argtypes = [_vp, _ip, _ip, _ip, _ip, ctypes.c_int]
+        L.pc_plans_import.restype = ctypes.c_int
         L.pc_compute_packed.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                         _vp, _vp, _vp]
         L.pc_compute_host_batch.argtypes = [_vp, ctypes.POINTER(pc_frame), ctypes.c_int, _vp]
@@ -166,6 +171,25 @@ def pc_plan_tile_height(ctx, H, W) -> int:
 
 def pc_plan_lanes_per_pixel(ctx, H, W) -> int:
     return load().pc_plan_lanes_per_pixel(ctx, H, W)
+
+
+def pc_plans_export(ctx):
+    """Returns the plans of ctx as a list of (H, W, tile_height, lanes_per_pixel),
+    oldest first (None for a NULL ctx)."""
+    L = load()
+    n = L.pc_plans_export(ctx, None, None, None, None, 0)
+    if n < 0:
+        return None
+    arrs = [(ctypes.c_int * max(n, 1))() for _ in range(4)]
+    n = L.pc_plans_export(ctx, *arrs, n)
+    return [tuple(int(a[i]) for a in arrs) for i in range(n)]
+
+
+def pc_plans_import(ctx, plans) -> int:
+    """Adds plans given as (H, W, tile_height, lanes_per_pixel) tuples."""
+    n = len(plans)
+    arrs = [(ctypes.c_int * max(n, 1))(*[p[k] for p in plans]) for k in range(4)]
+    return load().pc_plans_import(ctx, *arrs, n)
 
 
 def pc_destroy(ctx) -> int:
@@ -263,6 +287,36 @@ class Curvature:
 
     def lanes_per_pixel(self, H, W):
         return pc_plan_lanes_per_pixel(self.ctx, H, W)
+
+    def _plan_key(self, device_name):
+        p = self.params
+        return {"device": device_name, "window_radius": self.window_radius, "iterations": self.iterations,
+                "stride": p.stride, "normal_radius": p.normal_radius, "reject": p.reject, "kahan": p.kahan,
+                "lanes_per_pixel": p.lanes_per_pixel}
+
+    def save_plans(self, path, device_name=None):
+        """Writes this context's plans (pc_plans_export) to a JSON file, with
+        the GPU model and the parameters they were tuned for."""
+        import json
+        import torch
+        name = device_name or torch.cuda.get_device_name()
+        with open(path, "w") as f:
+            json.dump({"key": self._plan_key(name), "plans": pc_plans_export(self.ctx)}, f)
+
+    def load_plans(self, path, device_name=None) -> bool:
+        """Adds the plans of a file written by save_plans when they were tuned
+        for this GPU model and these parameters; returns whether it did."""
+        import json
+        import torch
+        name = device_name or torch.cuda.get_device_name()
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("key") != self._plan_key(name):
+            return False
+        st = pc_plans_import(self.ctx, [tuple(p) for p in d["plans"]])
+        if st != PC_OK:
+            raise PcError(st, "pc_plans_import", pc_last_error(self.ctx))
+        return True
 
     def batch(self, frames, stream=None):
         """pc_compute_batch over a list of (depth, (fx, fy, cx, cy), k1, k2, normal)

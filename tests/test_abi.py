@@ -253,3 +253,50 @@ def test_binding_fails_loudly_without_library(pc, monkeypatch, tmp_path):
     monkeypatch.setattr(b, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         b.load()
+
+
+def test_plans_export_import_without_gpu(pc, tmp_path):
+    """Plans are host state: imported plans steer the plan queries, export
+    returns them oldest first, bad entries add nothing, and a JSON file keyed
+    by GPU model and parameters carries them to another context."""
+    st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5)
+    try:
+        assert pc.pc_plans_export(ctx) == []
+        plans = [(48, 64, 2, 4), (120, 160, 4, 1), (480, 640, 8, 1), (24, 32, 1, 8)]
+        assert pc.pc_plans_import(ctx, plans) == pc.PC_OK
+        assert pc.pc_plans_export(ctx) == plans
+        for H, W, th, lanes in plans:
+            assert pc.pc_plan_tile_height(ctx, H, W) == th and pc.pc_plan_lanes_per_pixel(ctx, H, W) == lanes
+        for bad in ([(48, 64, 3, 1)], [(48, 64, 8, 2)], [(0, 64, 8, 1)], [(16385, 64, 8, 1)],
+                    [(10, 10, 8, 1), (48, 64, 4, 3)]):
+            assert pc.pc_plans_import(ctx, bad) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_plans_export(ctx) == plans           # nothing was added
+        more = [(10 + i, 20, 8, 1) for i in range(15)]
+        assert pc.pc_plans_import(ctx, more) == pc.PC_OK
+        kept = pc.pc_plans_export(ctx)
+        assert len(kept) == 16 and kept[-15:] == more and kept[0] == plans[-1]   # oldest forgotten first
+        assert pc.pc_plans_import(ctx, [(48, 64, 4, 2)]) == pc.PC_OK               # same size: replaced
+        assert pc.pc_plan_lanes_per_pixel(ctx, 48, 64) == 2
+    finally:
+        pc.pc_destroy(ctx)
+    assert pc.pc_plans_export(None) is None
+    assert pc.pc_plans_import(None, []) == pc.PC_ERR_INVALID_ARG
+    p = pc.pc_params_default()
+    p.kahan = 1
+    st, kctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5, p)
+    try:
+        assert pc.pc_plans_import(kctx, [(48, 64, 2, 4)]) == pc.PC_ERR_INVALID_ARG   # no lane groups there
+        assert pc.pc_plans_import(kctx, [(48, 64, 8, 1)]) == pc.PC_OK
+    finally:
+        pc.pc_destroy(kctx)
+    a = pc.Curvature(525.0, 525.0, 319.5, 239.5, window_radius=7, iterations=5)
+    pc.pc_plans_import(a.ctx, [(48, 64, 2, 4), (120, 160, 4, 1)])
+    path = tmp_path / "plans.json"
+    a.save_plans(path, device_name="GPU X")
+    b = pc.Curvature(525.0, 525.0, 319.5, 239.5, window_radius=7, iterations=5)
+    assert b.load_plans(path, device_name="GPU X") and b.lanes_per_pixel(48, 64) == 4
+    c = pc.Curvature(525.0, 525.0, 319.5, 239.5, window_radius=5, iterations=5)
+    assert not c.load_plans(path, device_name="GPU X") and pc.pc_plans_export(c.ctx) == []
+    assert not b.load_plans(path, device_name="GPU Y")
+    for x in (a, b, c):
+        x.close()
