@@ -70,11 +70,12 @@ def parse(argv=None):
                     help="requests of the serving trace (default: 20000 with --report serve, "
                          "2000 in the main run)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs"], default=None,
+    ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs", "table2"], default=None,
                     help="instead of the benchmark line: precision = error of each precision variant "
                          "against the FP64 oracle (one 640x480 frame, radii 3, 7, 11); serve = the "
                          "serving trace and a point at half capacity; accuracy = error against "
-                         "analytic ground truth; outputs = the organised outputs alone")
+                         "analytic ground truth; outputs = the organised outputs alone; table2 = the "
+                         "paper's timing grid (3 resolutions x 9x9, 21x21, sparse 37x37 windows)")
     return ap.parse_args(argv)
 
 
@@ -484,8 +485,68 @@ def precision_report(args):
     return rows
 
 
+# The paper's timing grid (Table 2): image sizes and patches; the 37 x 37 patch is
+# "sparsely sampled" without a stride, read here as every third pixel (radius 18).
+TABLE2_SIZES = [(480, 640), (424, 512), (240, 320)]
+TABLE2_WINDOWS = [("9x9", 4, 1), ("21x21", 10, 1), ("37x37 sparse (stride 3)", 18, 3)]
+
+
+def table2_report(args):
+    """Time per frame of the whole method on the paper's Table 2 grid, one
+    pc_compute launch per frame (as a per-frame timing) and batches of 32
+    frames (pc_compute_batch), T = 5 iterations (the paper states none)."""
+    import torch
+    import synth
+    import paper_1707_00385_gb300 as pc
+    from paper_1707_00385_gb300 import build as pcbuild
+    pcbuild.build()
+    rows = []
+    stream = torch.cuda.Stream()
+    for H, W in TABLE2_SIZES:
+        sc = [synth.kinect_scene(2000 + i, H=H, W=W, noise="tof" if (H, W) == (424, 512) else "kinect")
+              for i in range(4)]
+        frames = 32
+        depth = [torch.from_numpy(sc[i % 4].depth).cuda() for i in range(frames)]
+        outs = [(torch.empty((H, W), device="cuda"), torch.empty((H, W), device="cuda"),
+                 torch.empty((H, W, 3), device="cuda")) for _ in range(frames)]
+        for name, r, stride in TABLE2_WINDOWS:
+            c = pc.Curvature(*sc[0].intrinsics, window_radius=r, iterations=ITERS, stride=stride)
+            args_b = [(depth[i], sc[i % 4].intrinsics) + outs[i] for i in range(frames)]
+
+            def per_frame():
+                for i in range(frames):
+                    c(depth[i], *outs[i], stream=stream)
+
+            def batched():
+                c.batch(args_b, stream=stream)
+
+            res = {"size": f"{W}x{H}", "window": name, "window_radius": r, "stride": stride, "iterations": ITERS}
+            for key, fn in (("per_frame_ms", per_frame), ("batched_ms_per_frame", batched)):
+                with torch.cuda.stream(stream):
+                    for _ in range(3):
+                        fn()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                reps = 5
+                with torch.cuda.stream(stream):
+                    for _ in range(reps):
+                        fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res[key] = e0.elapsed_time(e1) / (reps * frames)
+            res["mpixel_per_s_batched"] = H * W / res["batched_ms_per_frame"] / 1e3
+            c.close()
+            rows.append(res)
+            print(json.dumps(res), flush=True)
+    return rows
+
+
 def main():
     args = parse()
+    if args.report == "table2":
+        table2_report(args)
+        return
     if args.report == "precision":
         precision_report(args)
         return
