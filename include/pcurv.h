@@ -213,15 +213,20 @@ pc_status pc_compute_batch_static(pc_ctx* ctx, const pc_frame* frames, int n, vo
  * are host addresses, page-locked for the copies to overlap; normal may be
  * NULL).  Frames are taken in order in chunks of at most
  * PC_HOST_CHUNK_PIXELS pixels or PC_MAX_BATCH frames (a larger frame is a
- * chunk of its own); each chunk's ranges are copied into one of two device
+ * chunk of its own; the first chunk takes at most an eighth of that, and over
+ * the last two chunks' worth of pixels each chunk takes half of what is left,
+ * so that the copies that nothing overlaps -- the first in, the last out --
+ * stay short); each chunk's ranges are copied into one of two device
  * staging slots owned by ctx, computed by one pc_compute_batch launch and its
- * results copied back.  Copies in, computation and copies out run on three
- * streams owned by ctx, ordered by events, so that the copies of one chunk
- * overlap the computation of the chunks beside it.  The work starts after
+ * results copied back.  Copies in, computation and copies out run on four
+ * streams owned by ctx (two for computation: chunks alternate between them,
+ * each with its own batch scratch, so that the next chunk's kernel can start
+ * while the last tiles of the previous one finish), ordered by events, so that
+ * the copies of one chunk overlap the computation of the chunks beside it.  The work starts after
  * what is already enqueued on `stream`, and `stream` waits for the last copy
  * out: once it is synchronised every result is on the host.  Host buffers
  * must stay valid until then.  Results equal pc_compute_batch's bit for bit.  The
- * ctx's batch scratch is used on the internal compute stream: do not run
+ * ctx's batch scratch is used on the internal compute streams: do not run
  * pc_compute_batch on the same ctx concurrently.  Staging slots grow to the
  * largest chunk seen (24 B per pixel each).  Errors: argument errors are
  * reported before anything is enqueued; a CUDA error in the middle of the

@@ -52,12 +52,14 @@ struct BatchScratch {
 };
 
 // Pipeline of pc_compute_host_batch: two device staging slots (each holds the
-// ranges and results of one chunk of frames) and three streams -- copies in,
-// compute, copies out -- ordered by events, so that the copies of one chunk
-// overlap the computation of its neighbours.
+// ranges and results of one chunk of frames) and four streams -- copies in,
+// two compute streams (chunks alternate between them, each with its own batch
+// scratch), copies out -- ordered by events, so that the copies of one chunk
+// overlap the computation of its neighbours and consecutive chunks' kernels
+// overlap where one ends and the next begins.
 struct HostPipe {
     int device = -1;
-    cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
+    cudaStream_t in = nullptr, comp[2] = {nullptr, nullptr}, out = nullptr;
     cudaEvent_t start = nullptr, tail = nullptr;
     cudaEvent_t in_done[2] = {nullptr, nullptr}, comp_done[2] = {nullptr, nullptr};
     cudaEvent_t slot_free[2] = {nullptr, nullptr};
@@ -87,6 +89,7 @@ struct pc_ctx {
     float* d_k2 = nullptr;
     float* d_normal = nullptr;
     BatchScratch batch;
+    BatchScratch batch_alt;                   // odd chunks of pc_compute_host_batch
     HostPipe pipe;
     Plan plans[16];
     long long plan_clock = 0;
@@ -550,9 +553,8 @@ pc_status pc_compute_host(pc_ctx* ctx, const float* depth_host, int H, int W, vo
     return PC_OK;
 }
 
-// Batch scratch for at least n frames on the current device.
-static pc_status ensure_batch(pc_ctx* ctx, int n) {
-    BatchScratch& b = ctx->batch;
+// Batch scratch b (of ctx) for at least n frames on the current device.
+static pc_status ensure_batch(pc_ctx* ctx, BatchScratch& b, int n) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetDevice");
@@ -585,8 +587,8 @@ static pc_status ensure_batch(pc_ctx* ctx, int n) {
 
 // Copy of the staged table, queue reset and persistent kernel (tile variant v,
 // `grid` CTAs), on `s`.
-static cudaError_t enqueue_batch(pc_ctx* ctx, int slot, size_t bytes, int v, int grid, cudaStream_t s) {
-    BatchScratch& b = ctx->batch;
+static cudaError_t enqueue_batch(pc_ctx* ctx, BatchScratch& b, int slot, size_t bytes, int v, int grid,
+                                 cudaStream_t s) {
     cudaError_t e = cudaMemcpyAsync(b.d_table, b.h_table[slot], bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
@@ -595,8 +597,7 @@ static cudaError_t enqueue_batch(pc_ctx* ctx, int slot, size_t bytes, int v, int
 
 // The graph of staging copy `slot` (captured on the private stream once per
 // capacity and tile variant).
-static pc_status ensure_graph(pc_ctx* ctx, int slot, int v) {
-    BatchScratch& b = ctx->batch;
+static pc_status ensure_graph(pc_ctx* ctx, BatchScratch& b, int slot, int v) {
     if (b.graph[slot] && b.graph_cap[slot] == b.cap && b.graph_grid[slot] == b.grid[v] &&
         b.graph_variant[slot] == v)
         return PC_OK;
@@ -605,7 +606,7 @@ static pc_status ensure_graph(pc_ctx* ctx, int slot, int v) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b.capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture begin");
-    const cudaError_t e1 = enqueue_batch(ctx, slot, pcurv::batch_table_bytes(b.cap), v, b.grid[v], b.capture);
+    const cudaError_t e1 = enqueue_batch(ctx, b, slot, pcurv::batch_table_bytes(b.cap), v, b.grid[v], b.capture);
     e = cudaStreamEndCapture(b.capture, &g);
     if (e1 != cudaSuccess || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -623,8 +624,8 @@ static pc_status ensure_graph(pc_ctx* ctx, int slot, int v) {
     return PC_OK;
 }
 
-pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream) {
-    const HostRange range("pc_compute_batch");
+// pc_compute_batch on batch scratch b of ctx.
+static pc_status batch_on(pc_ctx* ctx, BatchScratch& b, const pc_frame* frames, int n, void* stream) {
     if (!ctx || n < 0 || n > PC_MAX_BATCH || (n > 0 && !frames)) return PC_ERR_INVALID_ARG;
     long long total = 0;  // 32 x 8 tiles
     int live = 0;
@@ -640,9 +641,8 @@ pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* str
     }
     if (live == 0) return PC_OK;
     if (2 * total > 0x7fffffffLL) return PC_ERR_INVALID_ARG;
-    pc_status st = ensure_batch(ctx, live);
+    pc_status st = ensure_batch(ctx, b, live);
     if (st != PC_OK) return st;
-    BatchScratch& b = ctx->batch;
     const pcurv::KernelOps* ops = pcurv::select_ops(ctx->cfg);
     int v = forced_variant(ctx);
     if (v < 0) {
@@ -684,14 +684,19 @@ pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* str
     // launches bypass the graph, which holds the full grid.
     const int grid = begin < b.grid[v] ? begin : b.grid[v];
     if (ctx->params.batch_graph && grid == b.grid[v]) {
-        if ((st = ensure_graph(ctx, slot, v)) != PC_OK) return st;
+        if ((st = ensure_graph(ctx, b, slot, v)) != PC_OK) return st;
         if ((e = cudaGraphLaunch(b.graph[slot], s)) != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
-    } else if ((e = enqueue_batch(ctx, slot, pcurv::batch_table_bytes(live), v, grid, s)) != cudaSuccess) {
+    } else if ((e = enqueue_batch(ctx, b, slot, pcurv::batch_table_bytes(live), v, grid, s)) != cudaSuccess) {
         return cuda_fail(ctx, e, "batch launch");
     }
     if ((e = cudaEventRecord(b.done[slot], s)) != cudaSuccess) return cuda_fail(ctx, e, "batch event");
     b.pending[slot] = true;
     return PC_OK;
+}
+
+pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream) {
+    const HostRange range("pc_compute_batch");
+    return ctx ? batch_on(ctx, ctx->batch, frames, n, stream) : PC_ERR_INVALID_ARG;
 }
 
 static void release_pipe(HostPipe& p) {
@@ -712,7 +717,7 @@ static void release_pipe(HostPipe& p) {
     }
     delete[] p.dev_frames;
     p.dev_frames = nullptr;
-    for (cudaStream_t* st : {&p.in, &p.comp, &p.out}) {
+    for (cudaStream_t* st : {&p.in, &p.comp[0], &p.comp[1], &p.out}) {
         if (*st) cudaStreamDestroy(*st);
         *st = nullptr;
     }
@@ -728,7 +733,7 @@ static pc_status ensure_pipe(pc_ctx* ctx) {
     if (p.device == dev) return PC_OK;
     if (p.device >= 0) release_pipe(p);
     p.device = dev;
-    for (cudaStream_t* st : {&p.in, &p.comp, &p.out})
+    for (cudaStream_t* st : {&p.in, &p.comp[0], &p.comp[1], &p.out})
         if ((e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking)) != cudaSuccess) break;
     for (int i = 0; i < 2 && e == cudaSuccess; i++)
         for (cudaEvent_t* ev : {&p.in_done[i], &p.comp_done[i], &p.slot_free[i]})
@@ -770,16 +775,25 @@ pc_status pc_compute_host_batch(pc_ctx* ctx, const pc_frame* frames, int n, void
         return cuda_fail(ctx, e, "pipeline start");
     pc_frame* dev = p.dev_frames;
     int i = 0, chunk = 0;
+    size_t left = total_px;
     while (i < n) {
-        // next chunk: frames up to PC_HOST_CHUNK_PIXELS pixels (at least one frame)
+        // next chunk: frames up to a pixel limit (at least one frame).  The limit
+        // is PC_HOST_CHUNK_PIXELS, smaller at both ends, where copies are not
+        // hidden behind computation: the first chunk's copy in and the last
+        // one's copy out.  The first chunk takes an eighth; over the last two
+        // chunks' worth of pixels each chunk takes half of what is left.
+        const size_t full = (size_t)PC_HOST_CHUNK_PIXELS;
+        size_t cap = chunk == 0 ? full / 8 : full;
+        if (left <= 2 * full) cap = left / 2 > full / 16 ? left / 2 : full / 16;
         int j = i;
         size_t px = 0;
         while (j < n && j - i < PC_MAX_BATCH) {
             const size_t f = (size_t)frames[j].H * frames[j].W;
-            if (j > i && px + f > (size_t)PC_HOST_CHUNK_PIXELS) break;
+            if (j > i && px + f > cap) break;
             px += f;
             j++;
         }
+        left -= px;
         const int slot = chunk & 1;
         if (px > p.cap_px[slot]) {
             // grow: wait until the chunk that last used the slot has been copied out
@@ -812,11 +826,14 @@ pc_status pc_compute_host_batch(pc_ctx* ctx, const pc_frame* frames, int n, void
                                 fr.normal ? d_nrm + 3 * off : nullptr};
             off += f;
         }
+        // chunks alternate between two compute streams, each with its own batch
+        // scratch, so that a chunk's kernel can start on the SMs the previous
+        // chunk's last tiles leave idle
         if ((e = cudaEventRecord(p.in_done[slot], p.in)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(p.comp, p.in_done[slot], 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(p.comp[slot], p.in_done[slot], 0)) != cudaSuccess)
             return cuda_fail(ctx, e, "pipeline order");
-        if ((st = pc_compute_batch(ctx, dev, m, p.comp)) != PC_OK) return st;
-        if ((e = cudaEventRecord(p.comp_done[slot], p.comp)) != cudaSuccess ||
+        if ((st = batch_on(ctx, slot ? ctx->batch_alt : ctx->batch, dev, m, p.comp[slot])) != PC_OK) return st;
+        if ((e = cudaEventRecord(p.comp_done[slot], p.comp[slot])) != cudaSuccess ||
             (e = cudaStreamWaitEvent(p.out, p.comp_done[slot], 0)) != cudaSuccess)
             return cuda_fail(ctx, e, "pipeline order");
         off = 0;
@@ -883,6 +900,7 @@ pc_status pc_destroy(pc_ctx* ctx) {
     }
     if (ctx->pipe.device >= 0) release_pipe(ctx->pipe);
     if (ctx->batch.device >= 0) release_batch(ctx->batch);
+    if (ctx->batch_alt.device >= 0) release_batch(ctx->batch_alt);
     delete ctx;
     return PC_OK;
 }
