@@ -1,6 +1,5 @@
 """Behaviour of the C ABI on the GPU: edge cases of the input, the
 host-memory entry point, streams, determinism, and argument errors."""
-import ctypes
 
 import numpy as np
 import pytest

@@ -4,7 +4,6 @@ pixel rate.  Checks continuous batching, admission by the memory budget,
 batch limits, order, the latency bookkeeping, and failures injected on the
 host (refused frames, launches that raise, batches that report an error)."""
 import numpy as np
-import pytest
 
 from paper_1707_00385_gb300.serve import BYTES_PER_PIXEL, Request, Server, poisson_arrivals
 
