@@ -199,11 +199,16 @@ namespace {
 // translation unit with the lane-group variants, which take radius and stride
 // at run time for every window (pc_fit_lanes.cu: unrolled copies for each
 // radius would multiply the build time for frames that are small anyway).
+// Index 13: the sparse 37 x 37 patch (radius 18, stride 3).
 struct OpsTable {
-    KernelOps ops[13];
+    KernelOps ops[14];
     OpsTable() {
-        for (int i = 0; i <= 12; i++) {
-            const KernelOps* one = i == 0 ? ops_generic() : i <= 4 ? ops_r1_4(i) : i <= 8 ? ops_r5_8(i) : ops_r9_12(i);
+        for (int i = 0; i <= 13; i++) {
+            const KernelOps* one = i == 0    ? ops_generic()
+                                   : i <= 4  ? ops_r1_4(i)
+                                   : i <= 8  ? ops_r5_8(i)
+                                   : i <= 12 ? ops_r9_12(i)
+                                             : ops_sparse(SPARSE_RADIUS, SPARSE_STRIDE);
             const KernelOps* lanes = ops_lanes();
             ops[i] = *one;
             for (int v = 0; v < NUM_TILE_VARIANTS; v++) {
@@ -222,6 +227,7 @@ const KernelOps* select_ops(const FitConfig& cfg) {
     if (cfg.kahan) return ops_precision(1, 0);
     static const OpsTable table;  // built once (thread-safe initialisation)
     const bool dense = cfg.stride == 1 && cfg.r >= 1 && cfg.r <= 12;
+    if (cfg.r == SPARSE_RADIUS && cfg.stride == SPARSE_STRIDE) return &table.ops[13];
     return &table.ops[dense ? cfg.r : 0];
 }
 

@@ -406,9 +406,11 @@ __device__ __forceinline__ void rotate_left(float R[9], float t0, float t1) {
 // Visits every symmetric pair of the window of the thread's pixel once.
 // zc, cc point at the pixel's own entries of the Z and c planes (row stride SW).
 // Rows dv = -r0 .. -s pair with rows -dv; the centre row pairs du < 0 with -du.
-template <int RW, typename F>
+// RW > 0: radius RW and stride RS fixed at compile time (columns unrolled).
+template <int RW, int RS = 1, typename F>
 __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, int SW, int r, int s,
                                               F&& f) {
+    constexpr int R0 = RW > 0 ? (RW / RS) * RS : 0;  // largest sampled offset, compile-time form
     const int r0 = (r / s) * s;
     const f32x2 STEP = pack((float)s, -(float)s);
     for (int dv = -r0; dv < 0; dv += s) {
@@ -422,7 +424,7 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
 #else
 #pragma unroll
 #endif
-            for (int du = -RW; du <= RW; du++) {
+            for (int du = -R0; du <= R0; du += RS) {
                 f(za[du], zb[-du], ca[du], cb[-du], DU, DV);
                 DU = add2(DU, STEP);
             }
@@ -441,7 +443,7 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
 #else
 #pragma unroll
 #endif
-        for (int du = -RW; du < 0; du++) {
+        for (int du = -R0; du < 0; du += RS) {
             f(zc[du], zc[-du], cc[du], cc[-du], DU, DV0);
             DU = add2(DU, STEP);
         }
@@ -594,13 +596,13 @@ __device__ __forceinline__ bool initial_normal(const float* zc, int SW, int rn_r
 // of frame f.  Called by every thread of the CTA (32 x TH G threads, TH G
 // warps); contains one __syncthreads and leaves shared memory in use until it
 // returns (callers that reuse smem synchronise first).
-// RW > 0: window radius fixed at compile time, dense window, columns unrolled.
-// RW == 0: radius and stride from cfg.
+// RW > 0: window radius RW and sampling stride RS fixed at compile time,
+// columns unrolled.  RW == 0: radius and stride from cfg.
 // G: lanes per pixel.  G = 1: one thread per pixel.  G > 1: G adjacent lanes
 // share a pixel's window rows (for_each_pair_lanes) and sum their moments
 // (reduce_lanes) before each solve, which every lane of the group repeats;
 // only the order of the moment sums differs from G = 1.
-template <int RW, bool REJECT, int PREC = 0, int TH = 8, int G = 1>
+template <int RW, bool REJECT, int PREC = 0, int TH = 8, int G = 1, int RS = 1>
 __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cfg, int tx_, int ty_,
                                          float* smem) {
     constexpr bool KAHAN = (PREC & PREC_KAHAN) != 0;
@@ -608,6 +610,7 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
     constexpr int NW = TH * G;  // warps of the CTA
     static_assert(G == 1 || G == 2 || G == 4 || G == 8, "lanes per pixel");
     static_assert(G == 1 || (!KAHAN && FMT == 0), "lane groups run the plain FP32 form");
+    static_assert(G == 1 || RW == 0 || RS == 1, "lane groups with a compile-time window are dense");
     const float* __restrict__ depth = f.depth;
     const int H = f.H, W = f.W;
     const Camera cam = f.cam;
@@ -615,7 +618,7 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
     float* __restrict__ k2o = f.k2;
     float* __restrict__ nrmo = f.normal;
     const int r = RW > 0 ? RW : cfg.r;
-    const int s = RW > 0 ? 1 : cfg.stride;
+    const int s = RW > 0 ? RS : cfg.stride;
     const int r0 = (r / s) * s;   // largest sampled offset
     const int halo = r > cfg.rn ? r : cfg.rn;
     const int SW = TILE_W + 2 * halo;
@@ -767,7 +770,7 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
                 se += sq_residual2(k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1), mul2(DV, CY2));
             };
             if constexpr (G == 1) {
-                for_each_pair<RW>(zc, cc, SW, r, s, sq);
+                for_each_pair<RW, RS>(zc, cc, SW, r, s, sq);
             } else {
                 for_each_pair_lanes<RW, G>(zc, cc, SW, r, s, sub, sq);
                 se = lane_group_sum<G>(se);
@@ -792,11 +795,11 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
         };
         if (it == 0) {
             // A = B = C = 0 here: the cheaper first-iteration form
-            if constexpr (G == 1) for_each_pair<RW>(zc, cc, SW, r, s, first);
+            if constexpr (G == 1) for_each_pair<RW, RS>(zc, cc, SW, r, s, first);
             else for_each_pair_lanes<RW, G>(zc, cc, SW, r, s, sub, first);
             first_iteration_sums(m, comp);
         } else {
-            if constexpr (G == 1) for_each_pair<RW>(zc, cc, SW, r, s, later);
+            if constexpr (G == 1) for_each_pair<RW, RS>(zc, cc, SW, r, s, later);
             else for_each_pair_lanes<RW, G>(zc, cc, SW, r, s, sub, later);
         }
         if constexpr (G > 1) reduce_lanes<G>(m);
@@ -850,11 +853,11 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
 // one CTA per SM instead of spilling.
 #define PC_BLOCKS_OF(PREC) (((PREC) & PREC_KAHAN) ? 1 : PC_MIN_BLOCKS)
 
-template <int RW, bool REJECT, int PREC, int TH, int G>
+template <int RW, bool REJECT, int PREC, int TH, int G, int RS>
 __global__ void __launch_bounds__(TILE_W * TH * G, PC_BLOCKS_OF(PREC) * (8 / (TH * G)))
     k_fit(FrameArgs f, FitConfig cfg) {
     extern __shared__ float smem[];
-    fit_tile<RW, REJECT, PREC, TH, G>(f, cfg, blockIdx.x, blockIdx.y, smem);
+    fit_tile<RW, REJECT, PREC, TH, G, RS>(f, cfg, blockIdx.x, blockIdx.y, smem);
 }
 
 // Persistent form over many frames: the CTAs take (frame, tile) items from a
@@ -863,7 +866,7 @@ __global__ void __launch_bounds__(TILE_W * TH * G, PC_BLOCKS_OF(PREC) * (8 / (TH
 // still gets one item per SM -- then items gridDim.x, gridDim.x + 1, ... with
 // one atomic each.  The header and descriptors live in device memory
 // (BatchTable); *next_tile must be 0 at launch.
-template <int RW, bool REJECT, int PREC, int TH, int G>
+template <int RW, bool REJECT, int PREC, int TH, int G, int RS>
 __global__ void __launch_bounds__(TILE_W * TH * G, PC_BLOCKS_OF(PREC) * (8 / (TH * G)))
     k_fit_batch(const BatchTable* __restrict__ table, unsigned* __restrict__ next_tile, FitConfig cfg) {
     extern __shared__ float smem[];
@@ -880,7 +883,7 @@ __global__ void __launch_bounds__(TILE_W * TH * G, PC_BLOCKS_OF(PREC) * (8 / (TH
         }
         const int local = t - fr[lo].tile_begin, tiles_x = fr[lo].tiles_x;
         const int ty_ = local / tiles_x;
-        fit_tile<RW, REJECT, PREC, TH, G>(fr[lo].f, cfg, local - ty_ * tiles_x, ty_, smem);
+        fit_tile<RW, REJECT, PREC, TH, G, RS>(fr[lo].f, cfg, local - ty_ * tiles_x, ty_, smem);
         __syncthreads();  // shared memory and s_tile are reused by the next tile
         if (threadIdx.x == 0 && threadIdx.y == 0) s_tile = (int)(gridDim.x + atomicAdd(next_tile, 1u));
         __syncthreads();
@@ -888,46 +891,47 @@ __global__ void __launch_bounds__(TILE_W * TH * G, PC_BLOCKS_OF(PREC) * (8 / (TH
     }
 }
 
-template <int RW, int PREC, int TH, int G = 1>
+template <int RW, int PREC, int TH, int G = 1, int RS = 1>
 cudaError_t launch_fit_rw(const FrameArgs& f, const FitConfig& cfg, cudaStream_t stream) {
     const dim3 block(TILE_W, TH * G);
     const dim3 grid((f.W + TILE_W - 1) / TILE_W, (f.H + TH - 1) / TH);
     const size_t smem = fit_smem_bytes(cfg, TH);
     if (cfg.reject)
-        k_fit<RW, true, PREC, TH, G><<<grid, block, smem, stream>>>(f, cfg);
+        k_fit<RW, true, PREC, TH, G, RS><<<grid, block, smem, stream>>>(f, cfg);
     else
-        k_fit<RW, false, PREC, TH, G><<<grid, block, smem, stream>>>(f, cfg);
+        k_fit<RW, false, PREC, TH, G, RS><<<grid, block, smem, stream>>>(f, cfg);
     return cudaGetLastError();
 }
 
-template <int RW, int PREC, int TH, int G = 1>
+template <int RW, int PREC, int TH, int G = 1, int RS = 1>
 cudaError_t launch_batch_rw(const BatchTable* table, unsigned* next_tile, int grid, const FitConfig& cfg,
                             cudaStream_t stream) {
     const dim3 block(TILE_W, TH * G);
     const size_t smem = fit_smem_bytes(cfg, TH);
     if (cfg.reject)
-        k_fit_batch<RW, true, PREC, TH, G><<<grid, block, smem, stream>>>(table, next_tile, cfg);
+        k_fit_batch<RW, true, PREC, TH, G, RS><<<grid, block, smem, stream>>>(table, next_tile, cfg);
     else
-        k_fit_batch<RW, false, PREC, TH, G><<<grid, block, smem, stream>>>(table, next_tile, cfg);
+        k_fit_batch<RW, false, PREC, TH, G, RS><<<grid, block, smem, stream>>>(table, next_tile, cfg);
     return cudaGetLastError();
 }
 
-template <int RW, int PREC, int TH, int G = 1>
+template <int RW, int PREC, int TH, int G = 1, int RS = 1>
 cudaError_t occupancy_rw(const FitConfig& cfg, int* blocks_per_sm) {
     const size_t smem = fit_smem_bytes(cfg, TH);
     return cfg.reject ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            blocks_per_sm, k_fit_batch<RW, true, PREC, TH, G>, TILE_W * TH * G, smem)
+                            blocks_per_sm, k_fit_batch<RW, true, PREC, TH, G, RS>, TILE_W * TH * G, smem)
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            blocks_per_sm, k_fit_batch<RW, false, PREC, TH, G>, TILE_W * TH * G, smem);
+                            blocks_per_sm, k_fit_batch<RW, false, PREC, TH, G, RS>, TILE_W * TH * G, smem);
 }
 
-// The one-lane variants (32 x 8 and 32 x 4 tiles) of radius RW (RW = 0:
-// run-time radius); the lane-group entries stay empty.
-template <int RW, int PREC>
+// The one-lane variants (32 x 8 and 32 x 4 tiles) of radius RW sampled every
+// RS pixels (RW = 0: run-time radius and stride); the lane-group entries stay
+// empty.
+template <int RW, int PREC, int RS = 1>
 const KernelOps* make_ops() {
-    static const KernelOps k = {{launch_fit_rw<RW, PREC, 8>, launch_fit_rw<RW, PREC, 4>},
-                                {launch_batch_rw<RW, PREC, 8>, launch_batch_rw<RW, PREC, 4>},
-                                {occupancy_rw<RW, PREC, 8>, occupancy_rw<RW, PREC, 4>}};
+    static const KernelOps k = {{launch_fit_rw<RW, PREC, 8, 1, RS>, launch_fit_rw<RW, PREC, 4, 1, RS>},
+                                {launch_batch_rw<RW, PREC, 8, 1, RS>, launch_batch_rw<RW, PREC, 4, 1, RS>},
+                                {occupancy_rw<RW, PREC, 8, 1, RS>, occupancy_rw<RW, PREC, 4, 1, RS>}};
     return &k;
 }
 

@@ -116,6 +116,10 @@ const KernelOps* ops_r5_8(int r);
 const KernelOps* ops_r9_12(int r);
 const KernelOps* ops_generic();
 const KernelOps* ops_lanes();
+// The sparsely sampled 37 x 37 patch of Sec. 4.2.1 (radius 18, read as every
+// third pixel), unrolled like the dense radii; nullptr for other windows.
+constexpr int SPARSE_RADIUS = 18, SPARSE_STRIDE = 3;
+const KernelOps* ops_sparse(int r, int stride);
 
 // Run-time-radius kernels of the precision variants: compensated sums and/or
 // 16-bit range storage (format 0 float32, 1 FP16, 2 BF16).
