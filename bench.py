@@ -128,14 +128,19 @@ def measured_hbm_gbs():
 
 
 def kernel_sources_hash():
-    """hash of the files that define the fused kernels (device code and the
-    structures it reads); host-only files do not change the kernel"""
+    """hash of the code of the files that define the fused kernels (device
+    code and the structures it reads), without comments and blank space:
+    host-only files and comment edits do not change the kernel"""
+    import re
     d = os.path.join(ROOT, "paper_1707_00385_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(d)):
         if (f.startswith("pc_fit") and f.endswith((".cu", ".cuh"))) or f in ("pc_f32x2.cuh", "pc_internal.h"):
+            code = open(os.path.join(d, f)).read()
+            code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+            code = re.sub(r"//[^\n]*", " ", code)
             h.update(f.encode())
-            h.update(open(os.path.join(d, f), "rb").read())
+            h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,7 +1,7 @@
 // pc_fit.cuh -- the fused per-pixel curvature kernel (sm_103a).
 //
-// One CTA computes a 32 x th tile of output pixels (th = 8 or 4), one thread
-// per pixel.  The
+// One CTA computes a 32 x th tile of output pixels (th = 8 or 4 with one
+// thread per pixel; th = 4, 2, 1 with lane groups of 2, 4, 8 per pixel).  The
 // CTA first stages the tile's range values plus a halo of max(r, r_n) pixels
 // into shared memory as two planes, Z and c, c = 1 for a valid range and +inf
 // for none (outside the image, zero, negative or not finite), and counts the
@@ -13,8 +13,9 @@
 //   frame            Sec. 3.2.2 (minimal rotation to the normal, A=B=C=t_z=0)
 //   T iterations     Sec. 3.2.3: residuals of Eq. quad, Jacobian, weights of
 //                    Eq. weighting_function, the 6x6 system of
-//                    Eq. iter_reweighted_update solved by a Jacobi-scaled
-//                    LDL^T factorisation, Gauss-Newton update
+//                    Eq. iter_reweighted_update solved by an LDL^T
+//                    factorisation judged on its Jacobi-scaled pivots,
+//                    Gauss-Newton update
 //   eigen step       Sec. 3.1.2 (T1, T2 closed form), refined normal Sec. 3.2.4
 //
 // The hot loop visits every window point once per iteration.  Its arithmetic

@@ -1,5 +1,6 @@
 // The fused kernels with the window radius and sampling stride read at run
-// time (radii above the unrolled set, and sparse windows), both tile variants.
+// time (radii above the unrolled set, and sparse windows other than the
+// 37 x 37 patch), both one-lane tile variants.
 #include "pc_fit.cuh"
 
 namespace pcurv {

@@ -1,5 +1,5 @@
 // Instantiations of the fused kernels for window radii 9..12 (dense window),
-// both tile variants.
+// both one-lane tile variants.
 #include "pc_fit.cuh"
 
 namespace pcurv {

@@ -1,5 +1,5 @@
 // Instantiation of the fused kernels for the sparsely sampled 37 x 37 patch
-// (radius 18, every third pixel: 13 x 13 samples), both tile variants, with
+// (radius 18, every third pixel: 13 x 13 samples), both one-lane tile variants, with
 // the window unrolled like the dense radii.
 #include "pc_fit.cuh"
 

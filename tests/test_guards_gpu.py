@@ -76,7 +76,7 @@ def outputs(H, W, device="cuda"):
 
 CONFIGS = [(7, {}), (7, {"tile_height": 4}), (7, {"lanes_per_pixel": 2}), (7, {"lanes_per_pixel": 4}),
            (7, {"lanes_per_pixel": 8}), (1, {}), (12, {}), (15, {}), (7, {"stride": 3}), (5, {"reject": 1}),
-           (3, {"kahan": 1}), (7, {"fp64_solve_cond": 1e6, "pivot_tol": 1e-7})]
+           (18, {"stride": 3}), (3, {"kahan": 1}), (7, {"fp64_solve_cond": 1e6, "pivot_tol": 1e-7})]
 
 
 @pytest.mark.parametrize("r,params", CONFIGS, ids=[f"r{r}-" + "-".join(f"{k}{v}" for k, v in p.items())
