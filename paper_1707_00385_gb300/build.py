@@ -45,8 +45,19 @@ def _stale(out, deps):
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     """Compiles csrc/*.cu (one nvcc per file, in parallel) and links lib/libpcurv.so.
-    Returns the library path."""
+    Returns the library path.  Processes that build at the same time (ranks
+    of one job) take turns on a lock file in lib/."""
+    import fcntl
     os.makedirs(LIBDIR, exist_ok=True)
+    with open(os.path.join(LIBDIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build(force, verbose, ptxas_info)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build(force, verbose, ptxas_info):
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(INCLUDE, "pcurv.h"))
     srcs = sources()
