@@ -155,3 +155,43 @@ def test_argument_errors_leave_outputs_untouched(gpu):
     with pytest.raises(ValueError):
         c(torch.ones((16, 16), device="cuda", dtype=torch.float64))
     c.close()
+
+
+def test_contexts_on_concurrent_streams(gpu):
+    """Four contexts on four streams, each with per-frame, batch and host-batch
+    calls in flight at once, give the bits of the same calls run one after
+    another on the default stream."""
+    import torch
+    scenes = [synth.kinect_scene(60 + i, H=h, W=w) for i, (h, w) in
+              enumerate([(240, 320), (480, 640), (424, 512), (120, 160)])]
+
+    def work(c, s, stream):
+        d = torch.from_numpy(s.depth).cuda()
+        a = c(d, stream=stream)
+        frames = [(d, s.intrinsics, torch.empty_like(d), torch.empty_like(d),
+                   torch.empty(d.shape + (3,), device="cuda")) for _ in range(2)]
+        c.batch(frames, stream=stream)
+        hf = [(torch.from_numpy(s.depth).pin_memory(), s.intrinsics, torch.empty(d.shape).pin_memory(),
+               torch.empty(d.shape).pin_memory(), torch.empty(d.shape + (3,)).pin_memory())]
+        c.host_batch(hf, stream=stream)
+        return d, a, frames, hf
+
+    def results(out):
+        d, a, frames, hf = out
+        return ([t.cpu().numpy() for t in a] + [t.cpu().numpy() for f in frames for t in f[2:]] +
+                [t.numpy().copy() for t in hf[0][2:]])
+
+    ctxs = [gpu.Curvature(*s.intrinsics, window_radius=7, iterations=5) for s in scenes]
+    seq = []
+    for c, s in zip(ctxs, scenes):
+        out = work(c, s, None)
+        torch.cuda.synchronize()
+        seq.append(results(out))
+    streams = [torch.cuda.Stream() for _ in scenes]
+    outs = [work(c, s, st) for c, s, st in zip(ctxs, scenes, streams)]
+    torch.cuda.synchronize()
+    for out, ref in zip(outs, seq):
+        for x, y in zip(results(out), ref):
+            assert np.array_equal(x, y, equal_nan=True)
+    for c in ctxs:
+        c.close()
