@@ -103,7 +103,8 @@ typedef struct pc_params {
                             too small to fill the GPU with one thread per pixel; on large
                             images it costs throughput.  It changes only the order of the
                             moment sums, so results differ from one lane per pixel by single-
-                            precision rounding.  Needs tile_height = 0 and kahan = 0.  1 = one
+                            precision rounding (the lanes' tree of partial sums rounds less:
+                            more pixels agree with exact arithmetic).  Needs tile_height = 0 and kahan = 0.  1 = one
                             lane per pixel, even where pc_autotune found a lane group faster;
                             0 = the size's pc_autotune result, else one lane.  Default 0 */
 } pc_params;
