@@ -70,12 +70,14 @@ def parse(argv=None):
                     help="requests of the serving trace (default: 20000 with --report serve, "
                          "2000 in the main run)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs", "table2"], default=None,
+    ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs", "table2", "sweep"],
+                    default=None,
                     help="instead of the benchmark line: precision = error of each precision variant "
                          "against the FP64 oracle (one 640x480 frame, radii 3, 7, 11); serve = the "
                          "serving trace and a point at half capacity; accuracy = error against "
                          "analytic ground truth; outputs = the organised outputs alone; table2 = the "
-                         "paper's timing grid (3 resolutions x 9x9, 21x21, sparse 37x37 windows)")
+                         "paper's timing grid (3 resolutions x 9x9, 21x21, sparse 37x37 windows); sweep = "
+                         "throughput and FP32-roofline fraction for window radii 1..12 at 640x480")
     return ap.parse_args(argv)
 
 
@@ -547,8 +549,55 @@ def table2_report(args):
     return rows
 
 
+def sweep_report(args):
+    """Throughput and counted-FLOP fraction of the FP32 peak for dense window
+    radii 1..12 (the unrolled kernels), 640 x 480 frames, T = 5, one batch of
+    32 frame buffers per step (the headline's launch form at a quarter of its
+    size), CUDA events over 5 steps after 3 warm-up ones."""
+    import torch
+    import paper_1707_00385_gb300 as pc
+    from paper_1707_00385_gb300 import build as pcbuild
+    pcbuild.build()
+    sc = scenes(8)
+    intr = sc[0].intrinsics
+    F = 32
+    depth = [torch.from_numpy(sc[i % 8].depth).cuda() for i in range(F)]
+    outs = [(torch.empty((H, W), device="cuda"), torch.empty((H, W), device="cuda"),
+             torch.empty((H, W, 3), device="cuda")) for _ in range(F)]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * 2070e6
+    stream = torch.cuda.Stream()
+    rows = []
+    for r in range(1, 13):
+        c = pc.Curvature(*intr, window_radius=r, iterations=ITERS)
+        frames = [(depth[i], intr) + outs[i] for i in range(F)]
+        flop = sum(counted_flop(sc[i % 8].depth, r=r) for i in range(F))
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                c.batch(frames, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(5):
+                c.batch(frames, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        c.close()
+        res = {"window_radius": r, "window": f"{2 * r + 1}x{2 * r + 1}", "ms_per_frame": ms / F,
+               "mpixel_per_s": F * H * W / ms / 1e3, "counted_tflop_per_s": flop / ms / 1e9,
+               "frac_fp32_peak": flop / ms / 1e-3 / peak}
+        rows.append(res)
+        print(json.dumps(res), flush=True)
+    return rows
+
+
 def main():
     args = parse()
+    if args.report == "sweep":
+        sweep_report(args)
+        return
     if args.report == "table2":
         table2_report(args)
         return
