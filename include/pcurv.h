@@ -57,7 +57,7 @@ typedef enum pc_status {
     PC_ERR_CUDA = 2,        /* a CUDA call failed; see pc_last_error() */
     PC_ERR_OOM = 3,         /* device or host allocation failed */
     PC_ERR_TIMEOUT = 4,     /* reserved: a bounded device wait gave up */
-    PC_ERR_UNSUPPORTED = 5  /* parameter combination this build does not implement */
+    PC_ERR_UNSUPPORTED = 5  /* parameter combination the library does not implement */
 } pc_status;
 
 /* Limits checked by every call. */
