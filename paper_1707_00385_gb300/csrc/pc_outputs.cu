@@ -99,8 +99,10 @@ __global__ void __launch_bounds__(TILE_W * TH, 4 * 8 / TH)
     float* tz = smem;
     const int ub = blockIdx.x * TILE_W, vb = blockIdx.y * TH;
     const int tid = threadIdx.y * TILE_W + threadIdx.x;
+    // element i = sy SW + sx, advanced by NT per step without a division
+    const int dy = NT / SW, dx = NT - dy * SW;
+    int sy = tid / SW, sx = tid - sy * SW;
     for (int i = tid; i < SW * SH; i += NT) {
-        const int sy = i / SW, sx = i - sy * SW;
         const int gv = vb - rn + sy, gu = ub - rn + sx;
         float z = 0.f;
         if (gu >= 0 && gu < W && gv >= 0 && gv < H) {
@@ -108,6 +110,12 @@ __global__ void __launch_bounds__(TILE_W * TH, 4 * 8 / TH)
             if (range_ok(d)) z = d;
         }
         tz[i] = z;
+        sx += dx;
+        sy += dy;
+        if (sx >= SW) {
+            sx -= SW;
+            sy++;
+        }
     }
     __syncthreads();
     const int u0 = ub + threadIdx.x, v0 = vb + threadIdx.y;
