@@ -15,7 +15,7 @@ launch per frame; `uneven_batch` runs 64 frames of mixed resolutions
 against 64 plain launches; `e2e` is the metric through pc_compute_host_batch
 with pinned host buffers (host-to-device ranges and device-to-host k1, k2,
 normals inside the timed region, pipelined in chunks against the compute;
-`one_call_per_frame` is the unpipelined pc_compute_host); `outputs` times
+`one_call_per_frame` is pc_compute_host once per frame); `outputs` times
 the organised point cloud (pc_backproject, against the HBM peak) and the
 initial-normal field (pc_initial_normals); `roofline` reports the persistent
 kernel against the FP32 ALU peak; `cpu_baseline` times the FP64 oracle on a

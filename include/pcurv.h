@@ -130,10 +130,16 @@ pc_status pc_compute(pc_ctx* ctx, const float* depth, int H, int W, void* stream
 
 /* The same from and to HOST buffers: copies depth to device staging buffers
  * owned by ctx, computes, and copies k1, k2 (and normal when not NULL) back,
- * all enqueued on `stream`.  The host buffers must stay valid until the
- * stream is synchronised.  Staging buffers are (re)allocated on the current
- * device when a larger image arrives (PC_ERR_OOM if that fails); successive
- * calls on one ctx must use one stream, or synchronise in between. */
+ * all ordered on `stream` (the work starts after what `stream` already holds,
+ * and `stream` completes when the results are on the host).  An image of
+ * several waves of thread blocks goes in up to eight bands of tile rows whose
+ * copies in, kernels and copies out overlap, on streams owned by ctx; a
+ * smaller one runs on `stream` itself.  Results are those of pc_compute, bit
+ * for bit.  The host buffers must stay valid until the stream is
+ * synchronised; pinned buffers let the copies run asynchronously.  Staging
+ * buffers are (re)allocated on the current device when a larger image arrives
+ * (PC_ERR_OOM if that fails); successive calls on one ctx must use one
+ * stream, or synchronise in between. */
 pc_status pc_compute_host(pc_ctx* ctx, const float* depth_host, int H, int W, void* stream,
                           float* k1_host, float* k2_host, float* normal_host);
 

@@ -51,6 +51,9 @@ struct BatchScratch {
     int next = 0;                             // staging copy of the next call
 };
 
+// Most bands of one pc_compute_host frame (each about a wave of CTAs or more).
+constexpr int HOST_BANDS = 8;
+
 // Pipeline of pc_compute_host_batch: two device staging slots (each holds the
 // ranges and results of one chunk of frames) and four streams -- copies in,
 // two compute streams (chunks alternate between them, each with its own batch
@@ -67,6 +70,8 @@ struct HostPipe {
     float* buf[2] = {nullptr, nullptr};      // device, px * 6 floats per slot
     size_t cap_px[2] = {0, 0};
     pc_frame* dev_frames = nullptr;          // host: device descriptors of one chunk
+    // pc_compute_host: one frame in bands of tile rows on the same streams
+    cudaEvent_t band_in[HOST_BANDS] = {}, band_done[HOST_BANDS] = {};
 };
 
 // Tile variant chosen by pc_autotune for one image size.
@@ -95,6 +100,7 @@ struct pc_ctx {
     long long plan_clock = 0;
     int sms_device = -1;
     int sms = 0;                              // SMs of that device
+    int resident[pcurv::NUM_TILE_VARIANTS] = {};  // CTAs of each tile variant resident there (0: not queried)
     char last_error[256] = {0};
 };
 
@@ -250,8 +256,23 @@ cudaError_t sm_count(pc_ctx* ctx, int* sms) {
         if ((e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
             return e;
         ctx->sms_device = dev;
+        for (int& n : ctx->resident) n = 0;
     }
     *sms = ctx->sms;
+    return cudaSuccess;
+}
+
+// CTAs of tile variant v of ops that the current device holds at once (one wave).
+cudaError_t resident_ctas(pc_ctx* ctx, const pcurv::KernelOps* ops, int v, int* n) {
+    int sms = 0;
+    cudaError_t e = sm_count(ctx, &sms);
+    if (e != cudaSuccess) return e;
+    if (ctx->resident[v] == 0) {
+        int per_sm = 0;
+        if ((e = ops->occupancy[v](ctx->cfg, &per_sm)) != cudaSuccess) return e;
+        ctx->resident[v] = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    *n = ctx->resident[v];
     return cudaSuccess;
 }
 
@@ -285,6 +306,16 @@ cudaError_t variant_for(pc_ctx* ctx, const pcurv::KernelOps* ops, int H, int W, 
     }
     *v = ops->fit[choice] ? choice : 0;
     return cudaSuccess;
+}
+
+// Tile rows of an H-row frame in variant v, and one launch over all of them.
+int tile_rows(int H, int v) {
+    const int th = pcurv::tile_h_of(v);
+    return (H + th - 1) / th;
+}
+cudaError_t fit_frame(const pcurv::KernelOps* ops, int v, const pcurv::FrameArgs& f, const pcurv::FitConfig& cfg,
+                      cudaStream_t s) {
+    return ops->fit[v](f, cfg, s, 0, tile_rows(f.H, v));
 }
 
 void remember_plan(pc_ctx* ctx, int H, int W, int variant) {
@@ -356,7 +387,7 @@ pc_status pc_compute(pc_ctx* ctx, const float* depth, int H, int W, void* stream
     int v = 0;
     cudaError_t e = variant_for(ctx, ops, H, W, &v);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute plan");
-    e = ops->fit[v](f, ctx->cfg, (cudaStream_t)stream);
+    e = fit_frame(ops, v, f, ctx->cfg, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute launch");
     return PC_OK;
 }
@@ -382,9 +413,9 @@ pc_status pc_autotune(pc_ctx* ctx, const float* depth, int H, int W, void* strea
     float best_ms = 3.4e38f;
     for (int v = 0; v < pcurv::NUM_TILE_VARIANTS && e == cudaSuccess; v++) {
         if (!ops->fit[v] || !plan_allows(ctx, v)) continue;
-        e = ops->fit[v](f, ctx->cfg, s);
+        e = fit_frame(ops, v, f, ctx->cfg, s);
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-        for (int i = 0; i < 3 && e == cudaSuccess; i++) e = ops->fit[v](f, ctx->cfg, s);
+        for (int i = 0; i < 3 && e == cudaSuccess; i++) e = fit_frame(ops, v, f, ctx->cfg, s);
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -493,7 +524,7 @@ pc_status pc_compute_packed(pc_ctx* ctx, const unsigned short* packed, const flo
         return PC_ERR_INVALID_ARG;
     const pcurv::FrameArgs f{nullptr, H, W, ctx->cam, k1_out, k2_out, normal_out, packed, tile_base};
     const cudaError_t e =
-        pcurv::ops_precision(ctx->cfg.kahan, format)->fit[0](f, ctx->cfg, (cudaStream_t)stream);
+        fit_frame(pcurv::ops_precision(ctx->cfg.kahan, format), 0, f, ctx->cfg, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_packed launch");
     return PC_OK;
 }
@@ -506,6 +537,8 @@ static void free_stage(pc_ctx* ctx) {
     ctx->d_depth = ctx->d_k1 = ctx->d_k2 = ctx->d_normal = nullptr;
     ctx->stage_px = 0;
 }
+
+static pc_status ensure_pipe(pc_ctx* ctx);
 
 pc_status pc_compute_host(pc_ctx* ctx, const float* depth_host, int H, int W, void* stream,
                           float* k1_host, float* k2_host, float* normal_host) {
@@ -537,25 +570,88 @@ pc_status pc_compute_host(pc_ctx* ctx, const float* depth_host, int H, int W, vo
         ctx->stage_device = dev;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if ((e = cudaMemcpyAsync(ctx->d_depth, depth_host, npx * sizeof(float), cudaMemcpyHostToDevice,
-                             s)) != cudaSuccess)
-        return cuda_fail(ctx, e, "depth H2D");
     const pcurv::FrameArgs f{ctx->d_depth, H, W, ctx->cam, ctx->d_k1, ctx->d_k2,
                              normal_host ? ctx->d_normal : nullptr, nullptr, nullptr};
     const pcurv::KernelOps* ops = pcurv::select_ops(ctx->cfg);
     int v = 0;
     if ((e = variant_for(ctx, ops, H, W, &v)) != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_host plan");
-    e = ops->fit[v](f, ctx->cfg, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_host launch");
-    if ((e = cudaMemcpyAsync(k1_host, ctx->d_k1, npx * sizeof(float), cudaMemcpyDeviceToHost, s)) !=
-            cudaSuccess ||
-        (e = cudaMemcpyAsync(k2_host, ctx->d_k2, npx * sizeof(float), cudaMemcpyDeviceToHost, s)) !=
+    const int rows = tile_rows(H, v), th = pcurv::tile_h_of(v);
+    const long long tiles = (long long)rows * ((W + pcurv::TILE_W - 1) / pcurv::TILE_W);
+    // A frame of several waves of CTAs goes in bands of tile rows, each about
+    // a wave or more: band b's ranges are copied in (with the halo rows its
+    // windows read), its kernel runs, its results are copied out, on the
+    // pipeline's streams, so that only the first band's copy in and the last
+    // band's copy out are not hidden behind a kernel.  Consecutive bands'
+    // kernels alternate between two streams and overlap at their ends.
+    int wave = 0;
+    if ((e = resident_ctas(ctx, ops, v, &wave)) != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_host occupancy");
+    long long bands_ll = (2 * tiles + wave) / (2 * wave);  // bands of at least 7/8 of a wave
+    if (bands_ll > HOST_BANDS) bands_ll = HOST_BANDS;
+    if (bands_ll > rows) bands_ll = rows;
+    const int bands = (int)bands_ll;
+    if (bands <= 1) {
+        if ((e = cudaMemcpyAsync(ctx->d_depth, depth_host, npx * sizeof(float), cudaMemcpyHostToDevice, s)) !=
             cudaSuccess)
-        return cuda_fail(ctx, e, "curvature D2H");
-    if (normal_host &&
-        (e = cudaMemcpyAsync(normal_host, ctx->d_normal, 3 * npx * sizeof(float),
-                             cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_fail(ctx, e, "normal D2H");
+            return cuda_fail(ctx, e, "depth H2D");
+        if ((e = fit_frame(ops, v, f, ctx->cfg, s)) != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_host launch");
+        if ((e = cudaMemcpyAsync(k1_host, ctx->d_k1, npx * sizeof(float), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(k2_host, ctx->d_k2, npx * sizeof(float), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess)
+            return cuda_fail(ctx, e, "curvature D2H");
+        if (normal_host &&
+            (e = cudaMemcpyAsync(normal_host, ctx->d_normal, 3 * npx * sizeof(float),
+                                 cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "normal D2H");
+        return PC_OK;
+    }
+    if ((st = ensure_pipe(ctx)) != PC_OK) return st;
+    HostPipe& p = ctx->pipe;
+    // start after the caller's earlier work and after every earlier host
+    // call's copies out (the staging buffers are reused)
+    if ((e = cudaEventRecord(p.start, s)) != cudaSuccess || (e = cudaStreamWaitEvent(p.in, p.start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p.in, p.tail, 0)) != cudaSuccess)
+        return cuda_fail(ctx, e, "pc_compute_host start");
+    const int halo = pcurv::halo_of(ctx->cfg);
+    int copied = 0;  // rows of ranges enqueued so far
+    for (int b = 0; b < bands; b++) {
+        const int ty0 = (int)((long long)rows * b / bands), ty1 = (int)((long long)rows * (b + 1) / bands);
+        const int last = ty1 * th + halo;
+        const int need = b + 1 < bands && last < H ? last : H;
+        if (need > copied) {
+            if ((e = cudaMemcpyAsync(ctx->d_depth + (size_t)copied * W, depth_host + (size_t)copied * W,
+                                     (size_t)(need - copied) * W * sizeof(float), cudaMemcpyHostToDevice, p.in)) !=
+                cudaSuccess)
+                return cuda_fail(ctx, e, "depth H2D");
+            copied = need;
+        }
+        cudaStream_t c = p.comp[b & 1];
+        if ((e = cudaEventRecord(p.band_in[b], p.in)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(c, p.band_in[b], 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "pc_compute_host order");
+        if ((e = ops->fit[v](f, ctx->cfg, c, ty0, ty1)) != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_host launch");
+        if ((e = cudaEventRecord(p.band_done[b], c)) != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_host order");
+    }
+    // copies out after all kernels are enqueued (a copy to pageable memory may block the host)
+    for (int b = 0; b < bands; b++) {
+        const int v0 = (int)((long long)rows * b / bands) * th;
+        const int v1e = (int)((long long)rows * (b + 1) / bands) * th, v1 = v1e < H ? v1e : H;
+        const size_t o = (size_t)v0 * W, n = (size_t)(v1 - v0) * W;
+        if ((e = cudaStreamWaitEvent(p.out, p.band_done[b], 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "pc_compute_host order");
+        if ((e = cudaMemcpyAsync(k1_host + o, ctx->d_k1 + o, n * sizeof(float), cudaMemcpyDeviceToHost, p.out)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(k2_host + o, ctx->d_k2 + o, n * sizeof(float), cudaMemcpyDeviceToHost, p.out)) !=
+                cudaSuccess)
+            return cuda_fail(ctx, e, "curvature D2H");
+        if (normal_host &&
+            (e = cudaMemcpyAsync(normal_host + 3 * o, ctx->d_normal + 3 * o, 3 * n * sizeof(float),
+                                 cudaMemcpyDeviceToHost, p.out)) != cudaSuccess)
+            return cuda_fail(ctx, e, "normal D2H");
+    }
+    // the caller's stream completes when the last results are on the host
+    if ((e = cudaEventRecord(p.tail, p.out)) != cudaSuccess || (e = cudaStreamWaitEvent(s, p.tail, 0)) != cudaSuccess)
+        return cuda_fail(ctx, e, "pc_compute_host end");
     return PC_OK;
 }
 
@@ -721,6 +817,11 @@ static void release_pipe(HostPipe& p) {
         if (*ev) cudaEventDestroy(*ev);
         *ev = nullptr;
     }
+    for (int b = 0; b < HOST_BANDS; b++)
+        for (cudaEvent_t* ev : {&p.band_in[b], &p.band_done[b]}) {
+            if (*ev) cudaEventDestroy(*ev);
+            *ev = nullptr;
+        }
     delete[] p.dev_frames;
     p.dev_frames = nullptr;
     for (cudaStream_t* st : {&p.in, &p.comp[0], &p.comp[1], &p.out}) {
@@ -746,6 +847,9 @@ static pc_status ensure_pipe(pc_ctx* ctx) {
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     for (cudaEvent_t* ev : {&p.start, &p.tail})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    for (int b = 0; b < HOST_BANDS; b++)
+        for (cudaEvent_t* ev : {&p.band_in[b], &p.band_done[b]})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         p.dev_frames = new (std::nothrow) pc_frame[PC_MAX_BATCH];
         if (!p.dev_frames) e = cudaErrorMemoryAllocation;

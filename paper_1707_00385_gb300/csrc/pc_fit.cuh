@@ -854,11 +854,13 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
 // one CTA per SM instead of spilling.
 #define PC_BLOCKS_OF(PREC) (((PREC) & PREC_KAHAN) ? 1 : PC_MIN_BLOCKS)
 
+// One CTA per tile; grid row y computes tile row ty0 + y of the frame (a band
+// of tile rows when ty0 > 0 or the grid is shorter than the frame).
 template <int RW, bool REJECT, int PREC, int TH, int G, int RS>
 __global__ void __launch_bounds__(TILE_W * TH * G, PC_BLOCKS_OF(PREC) * (8 / (TH * G)))
-    k_fit(FrameArgs f, FitConfig cfg) {
+    k_fit(FrameArgs f, FitConfig cfg, int ty0) {
     extern __shared__ float smem[];
-    fit_tile<RW, REJECT, PREC, TH, G, RS>(f, cfg, blockIdx.x, blockIdx.y, smem);
+    fit_tile<RW, REJECT, PREC, TH, G, RS>(f, cfg, blockIdx.x, ty0 + blockIdx.y, smem);
 }
 
 // Persistent form over many frames: the CTAs take (frame, tile) items from a
@@ -892,15 +894,16 @@ __global__ void __launch_bounds__(TILE_W * TH * G, PC_BLOCKS_OF(PREC) * (8 / (TH
     }
 }
 
+// Tile rows ty0 .. ty1 - 1 of the frame (0 <= ty0 < ty1 <= its tile rows).
 template <int RW, int PREC, int TH, int G = 1, int RS = 1>
-cudaError_t launch_fit_rw(const FrameArgs& f, const FitConfig& cfg, cudaStream_t stream) {
+cudaError_t launch_fit_rw(const FrameArgs& f, const FitConfig& cfg, cudaStream_t stream, int ty0, int ty1) {
     const dim3 block(TILE_W, TH * G);
-    const dim3 grid((f.W + TILE_W - 1) / TILE_W, (f.H + TH - 1) / TH);
+    const dim3 grid((f.W + TILE_W - 1) / TILE_W, ty1 - ty0);
     const size_t smem = fit_smem_bytes(cfg, TH);
     if (cfg.reject)
-        k_fit<RW, true, PREC, TH, G, RS><<<grid, block, smem, stream>>>(f, cfg);
+        k_fit<RW, true, PREC, TH, G, RS><<<grid, block, smem, stream>>>(f, cfg, ty0);
     else
-        k_fit<RW, false, PREC, TH, G, RS><<<grid, block, smem, stream>>>(f, cfg);
+        k_fit<RW, false, PREC, TH, G, RS><<<grid, block, smem, stream>>>(f, cfg, ty0);
     return cudaGetLastError();
 }
 

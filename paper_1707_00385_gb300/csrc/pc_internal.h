@@ -102,7 +102,8 @@ inline size_t batch_table_bytes(int nframes) {
 // Kernel entry points of one instantiation (window radius, dense or run-time),
 // per tile variant (nullptr where a variant is not compiled).
 struct KernelOps {
-    cudaError_t (*fit[NUM_TILE_VARIANTS])(const FrameArgs&, const FitConfig&, cudaStream_t);
+    // tile rows [ty0, ty1) of one frame (the variant's tile height)
+    cudaError_t (*fit[NUM_TILE_VARIANTS])(const FrameArgs&, const FitConfig&, cudaStream_t, int ty0, int ty1);
     cudaError_t (*batch[NUM_TILE_VARIANTS])(const BatchTable*, unsigned*, int, const FitConfig&, cudaStream_t);
     cudaError_t (*occupancy[NUM_TILE_VARIANTS])(const FitConfig&, int*);
 };

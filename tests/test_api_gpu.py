@@ -116,6 +116,39 @@ def test_host_entry_matches_device_entry(gpu):
     c2.close()
 
 
+@pytest.mark.parametrize("H,W,r,params", [(480, 640, 7, {}), (720, 1280, 7, {}), (480, 640, 7, {"lanes_per_pixel": 2}),
+                                          (2000, 160, 7, {}), (480, 640, 12, {}), (480, 640, 3, {"tile_height": 4})])
+def test_host_entry_in_bands_matches_device_entry(gpu, H, W, r, params):
+    """Frames of several waves of CTAs go through pc_compute_host in bands of
+    tile rows (copies overlapping the kernels): the same bits as pc_compute,
+    for two frames enqueued back to back on one stream (the second reuses the
+    staging buffers the first is still copying out of) and without normals."""
+    import torch
+    frames = [synth.kinect_scene(40 + j, H=H, W=W) for j in range(2)]
+    c = gpu.Curvature(*frames[0].intrinsics, window_radius=r, iterations=5, **params)
+    ref = []
+    for s in frames:
+        k1, k2, n = c(torch.from_numpy(s.depth).cuda())
+        ref.append((k1.cpu().numpy(), k2.cpu().numpy(), n.cpu().numpy()))
+    hd = [torch.from_numpy(s.depth).pin_memory() for s in frames]
+    out = [(torch.empty(H, W).pin_memory(), torch.empty(H, W).pin_memory(), torch.empty(H, W, 3).pin_memory())
+           for _ in frames]
+    stream = torch.cuda.Stream()
+    for d, (hk1, hk2, hn) in zip(hd, out):
+        c.compute_host(d, hk1, hk2, hn, stream=stream)
+    stream.synchronize()
+    for (a1, a2, an), (hk1, hk2, hn) in zip(ref, out):
+        assert np.array_equal(hk1.numpy(), a1, equal_nan=True)
+        assert np.array_equal(hk2.numpy(), a2, equal_nan=True)
+        assert np.array_equal(hn.numpy(), an, equal_nan=True)
+    hk1, hk2 = torch.full((H, W), 3.0).pin_memory(), torch.full((H, W), 3.0).pin_memory()
+    c.compute_host(hd[1], hk1, hk2, None, stream=stream)
+    stream.synchronize()
+    assert np.array_equal(hk1.numpy(), ref[1][0], equal_nan=True)
+    assert np.array_equal(hk2.numpy(), ref[1][1], equal_nan=True)
+    c.close()
+
+
 def test_without_normals_and_determinism(gpu):
     import torch
     s = synth.crop(synth.kinect_scene(4), 200, 300, 40, 64)

@@ -131,13 +131,16 @@ def test_host_entry_points_stay_in_bounds(gpu, frames):
     torch.cuda.synchronize()
     for (d, k1, k2, n), hw in zip(held, frames):
         assert k1.intact() and k2.intact() and n.intact(), hw
-    (H, W), s = list(frames.items())[-1]
-    d = torch.from_numpy(s.depth).pin_memory()
-    k1, k2, n = outputs(H, W, device="cpu")
-    assert gpu.pc_compute_host(c, d.data_ptr(), H, W, None, k1.ptr, k2.ptr, n.ptr) == gpu.PC_OK
-    torch.cuda.synchronize()
+    # one small frame (one launch) and frames of several waves (bands of tile rows)
+    for s in (list(frames.values())[-1], synth.kinect_scene(5, H=480, W=640), synth.kinect_scene(6, H=1003, W=517)):
+        H, W = s.depth.shape
+        d = torch.from_numpy(s.depth).pin_memory()
+        k1, k2, n = outputs(H, W, device="cpu")
+        assert gpu.pc_compute_host(c, d.data_ptr(), H, W, None, k1.ptr, k2.ptr, n.ptr) == gpu.PC_OK
+        torch.cuda.synchronize()
+        assert k1.intact() and k2.intact() and n.intact(), (H, W)
+        assert k1.written() and n.written(), (H, W)
     gpu.pc_destroy(c)
-    assert k1.intact() and k2.intact() and n.intact()
 
 
 @pytest.mark.parametrize("fmt", [1, 2])
