@@ -311,9 +311,14 @@ def serve_trace(scenes_, n, rate, seed, batched=True, plain=True):
            "budget_bytes": budget}
     modes = ([("continuous_batching", GpuExecutor, dict(max_batch_frames=64, inflight=2))] if batched else []) + \
             ([("one_launch_per_frame", PlainExecutor, dict(max_batch_frames=1, inflight=64))] if plain else [])
+    # untimed start-up: a trace of the same rate (another seed) first, which
+    # also fills the executor's pool of page-locked result buffers
+    nw = min(n, 2000)
+    tw = poisson_arrivals(nw, rate, seed + 1000)
+    pick_w = np.random.default_rng(seed + 1000).integers(0, len(pool), nw)
     for name, Ex, kw in modes:
         ex = Ex(RADIUS, ITERS)
-        warm = [Request(-1 - i, *pool[i % len(pool)], 0.0) for i in range(len(pool))]
+        warm = [Request(-1 - i, *pool[pick_w[i]], float(tw[i])) for i in range(nw)]
         Server(ex, budget, **kw).run(warm)
         reqs = [Request(i, *pool[pick[i]], float(t[i])) for i in range(n)]
         st = Server(ex, budget, **kw).run(reqs)
