@@ -29,7 +29,12 @@ def build(force: bool = False) -> str:
     """Compile pc_oracle.c into liboracle.so next to it (OpenMP when available).
 
     -ffp-contract=off keeps every double operation separately rounded, so the
-    x86 and Arm builds give the same numbers."""
+    x86 and Arm builds give the same numbers.  PC_ORACLE_LIB names another
+    build to load instead (the test that plants mistakes in a copy of the
+    source runs the pins against that copy)."""
+    override = os.environ.get("PC_ORACLE_LIB")
+    if override:
+        return override
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     base = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-D_DEFAULT_SOURCE",
