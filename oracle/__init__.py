@@ -55,6 +55,7 @@ class Params(ctypes.Structure):
         ("k", ctypes.c_double), ("reject", ctypes.c_int), ("reject_ratio", ctypes.c_double),
         ("det_tol", ctypes.c_double), ("pivot_tol", ctypes.c_double), ("min_window", ctypes.c_int),
         ("perturb", ctypes.c_double), ("perturb_points", ctypes.c_double), ("perturb_seed", ctypes.c_ulonglong),
+        ("f32_sums", ctypes.c_int),
     ]
 
 
@@ -65,6 +66,7 @@ class Result(ctypes.Structure):
         ("normal", ctypes.c_double * 3), ("n0", ctypes.c_double * 3),
         ("A", ctypes.c_double), ("B", ctypes.c_double), ("C", ctypes.c_double), ("tz", ctypes.c_double),
         ("R", ctypes.c_double * 9), ("min_pivot", ctypes.c_double), ("last_b", ctypes.c_double * 6),
+        ("cond", ctypes.c_double),
     ]
 
 
@@ -77,10 +79,13 @@ MIN_WINDOW = 6
 
 def params(fx, fy, cx, cy, r, T, *, rn=3, k=1e-4, stride=1, reject=0, reject_ratio=2.0,
            det_tol=DET_TOL, pivot_tol=PIVOT_TOL, min_window=MIN_WINDOW, perturb=0.0,
-           perturb_points=0.0, perturb_seed=0) -> Params:
+           perturb_points=0.0, perturb_seed=0, f32_sums=0) -> Params:
+    """f32_sums = 1 is the probe's calibration mode, not the method: p' and
+    every sum of the normal equations and of the initial-normal regression
+    rounded to single precision (plain loop order)."""
     return Params(float(fx), float(fy), float(cx), float(cy), int(r), int(rn), int(T), int(stride),
                   float(k), int(reject), float(reject_ratio), float(det_tol), float(pivot_tol),
-                  int(min_window), float(perturb), float(perturb_points), int(perturb_seed))
+                  int(min_window), float(perturb), float(perturb_points), int(perturb_seed), int(f32_sums))
 
 
 _lib = None
@@ -96,6 +101,7 @@ def lib():
         L = ctypes.CDLL(build())
         L.or_backproject.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
         L.or_initial_normal.argtypes = [_D, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _D]
+        L.or_regression_sums.argtypes = [_D, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _D]
         L.or_frame_from_normal.argtypes = [_D, _D]
         L.or_rotation_exp.argtypes = [_D, _D]
         L.or_residual.argtypes = [_D] + [ctypes.c_double] * 4 + [_D, _D, _D]
@@ -111,10 +117,11 @@ def lib():
         L.or_fit_pixel_f32.argtypes = [_F, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(Result)]
         for name, dp in (("or_curvature_image", _F), ("or_curvature_image_f64", _D)):
-            getattr(L, name).argtypes = [dp, ctypes.c_int, ctypes.c_int, _P, _D, _D, _D, _I, _D, _D, ctypes.c_int]
+            getattr(L, name).argtypes = [dp, ctypes.c_int, ctypes.c_int, _P, _D, _D, _D, _I, _D, _D, _D,
+                                         ctypes.c_int]
         for name, dp in (("or_curvature_pixels", _F), ("or_curvature_pixels_f64", _D)):
             getattr(L, name).argtypes = [dp, ctypes.c_int, ctypes.c_int, _P, _I, ctypes.c_int,
-                                         _D, _D, _D, _I, _D, _D, ctypes.c_int]
+                                         _D, _D, _D, _I, _D, _D, _D, ctypes.c_int]
         L.or_max_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -149,6 +156,16 @@ def initial_normal(depth, p: Params, u0: int, v0: int):
     n = np.zeros(3)
     st = lib().or_initial_normal(_dp(d), d.shape[0], d.shape[1], ctypes.byref(p), u0, v0, _dp(n))
     return st, n
+
+
+def regression_sums(depth, p: Params, u0: int, v0: int):
+    """(count, sums) of the initial-normal regression of one pixel without the
+    probe: sums = (M00, M01, M11, v0, v1, sum of squared centred heights);
+    single precision when p.f32_sums (the probe's calibration)."""
+    d = _as_f64(depth)
+    sums = np.zeros(6)
+    cnt = lib().or_regression_sums(_dp(d), d.shape[0], d.shape[1], ctypes.byref(p), u0, v0, _dp(sums))
+    return cnt, sums
 
 
 def frame_from_normal(n) -> np.ndarray:
@@ -228,6 +245,7 @@ class Field:
     status: np.ndarray
     min_pivot: np.ndarray
     last_b: np.ndarray      # update b of the last iteration, (..., 6)
+    cond: np.ndarray = None  # largest max/min scaled-pivot ratio of one iteration (inf: singular)
 
     def converged(self, step_k=1e-5, step_theta=1e-6):
         """Pixels whose last Gauss-Newton update is below step_k * (1 + |k1|)
@@ -267,16 +285,16 @@ def curvature_image(depth, p: Params, nthreads: int = 0) -> Field:
     H, W = depth.shape
     k1, k2 = np.zeros((H, W)), np.zeros((H, W))
     nrm, st, mp = np.zeros((H, W, 3)), np.zeros((H, W), dtype=np.int32), np.zeros((H, W))
-    lb = np.zeros((H, W, 6))
+    lb, cd = np.zeros((H, W, 6)), np.zeros((H, W))
     if depth.dtype == np.float32:
         d = np.ascontiguousarray(depth)
         lib().or_curvature_image(d.ctypes.data_as(_F), H, W, ctypes.byref(p), _dp(k1), _dp(k2), _dp(nrm),
-                                 _ip(st), _dp(mp), _dp(lb), nthreads)
+                                 _ip(st), _dp(mp), _dp(lb), _dp(cd), nthreads)
     else:
         d = _as_f64(depth)
         lib().or_curvature_image_f64(_dp(d), H, W, ctypes.byref(p), _dp(k1), _dp(k2), _dp(nrm), _ip(st),
-                                     _dp(mp), _dp(lb), nthreads)
-    return Field(k1, k2, nrm, st, mp, lb)
+                                     _dp(mp), _dp(lb), _dp(cd), nthreads)
+    return Field(k1, k2, nrm, st, mp, lb, cd)
 
 
 def curvature_pixels(depth, p: Params, uv, nthreads: int = 0) -> Field:
@@ -287,13 +305,13 @@ def curvature_pixels(depth, p: Params, uv, nthreads: int = 0) -> Field:
     n = uv.shape[0]
     k1, k2 = np.zeros(n), np.zeros(n)
     nrm, st, mp = np.zeros((n, 3)), np.zeros(n, dtype=np.int32), np.zeros(n)
-    lb = np.zeros((n, 6))
+    lb, cd = np.zeros((n, 6)), np.zeros(n)
     if depth.dtype == np.float32:
         d = np.ascontiguousarray(depth)
         lib().or_curvature_pixels(d.ctypes.data_as(_F), H, W, ctypes.byref(p), _ip(uv), n, _dp(k1), _dp(k2),
-                                  _dp(nrm), _ip(st), _dp(mp), _dp(lb), nthreads)
+                                  _dp(nrm), _ip(st), _dp(mp), _dp(lb), _dp(cd), nthreads)
     else:
         d = _as_f64(depth)
         lib().or_curvature_pixels_f64(_dp(d), H, W, ctypes.byref(p), _ip(uv), n, _dp(k1), _dp(k2), _dp(nrm),
-                                      _ip(st), _dp(mp), _dp(lb), nthreads)
-    return Field(k1, k2, nrm, st, mp, lb)
+                                      _ip(st), _dp(mp), _dp(lb), _dp(cd), nthreads)
+    return Field(k1, k2, nrm, st, mp, lb, cd)

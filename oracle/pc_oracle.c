@@ -80,6 +80,9 @@ typedef struct {
                               the initial-normal sums (0 = off) */
     double perturb_points; /* sensitivity probe: relative noise on each p' coordinate (0 = off) */
     unsigned long long perturb_seed;
+    int f32_sums;          /* calibration of the probe, not the method: 1 = p' rounded to single
+                              precision and every sum of the normal equations and of the
+                              initial-normal regression added in single precision */
 } or_params;
 
 typedef struct {
@@ -93,6 +96,8 @@ typedef struct {
     double R[9];         /* final rotation, row major, camera -> local */
     double min_pivot;    /* smallest scaled Cholesky pivot over all iterations */
     double last_b[6];    /* the update b of the last iteration (0 when T = 0) */
+    double cond;         /* condition estimate: largest ratio of the largest to the smallest
+                            scaled Cholesky pivot of one iteration, over all iterations */
 } or_result;
 
 /* ------------------------------------------------------------------------ */
@@ -164,22 +169,32 @@ static double noise_at(unsigned long long key) {
     return (double)(splitmix64(key) >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
-/* The probe multiplies chosen intermediate values by 1 + a x, x uniform in
- * [-1, 1) keyed by (pixel, iteration, entry, seed): each entry of the
- * symmetric normal matrix and of the right-hand side (a = perturb), the
- * sums M and v of the initial-normal regression (a = perturb) and each
- * coordinate of p' (a = perturb_points).  The method's output under this noise
- * tells how much rounding of that relative size can move it: the tests use it
- * to find the pixels whose answer is fixed at single precision. */
-static void perturb_system(const or_params* p, unsigned long long key, double N[36], double rhs[6]) {
+/* The probe adds noise a x |scale| to chosen intermediate values, x uniform
+ * in [-1, 1) keyed by (pixel, iteration, entry, seed).  The scale of each
+ * entry is the bound that summation in floating point obeys (the rounding of
+ * a sum of terms t_i is at most a multiple of u sum |t_i|), with sum |t_i|
+ * bounded by Cauchy-Schwarz in terms of the diagonal: for the normal matrix
+ * N = J^T W J, sum |w j_a j_c| <= sqrt(N_aa N_cc); for the right-hand side
+ * sum |w eps j_a| <= sqrt(N_aa E), E = sum w eps^2; likewise for the sums M
+ * and v of the initial-normal regression (v with the sum of squared centred
+ * heights).  So entry (a, c) moves by up to a sqrt(N_aa N_cc): relative to
+ * the Jacobi-scaled matrix D N D, D = diag(N)^-1/2, that the solve factorises,
+ * every entry moves by up to a (a = perturb).  Each coordinate of p' is
+ * multiplied by 1 + a' x (a' = perturb_points).  The method's output under
+ * this noise tells how far rounding of that size can move it: the tests use
+ * it to find the pixels whose answer is fixed at single precision. */
+static void perturb_system(const or_params* p, unsigned long long key, double N[36], double rhs[6],
+                           double E) {
     if (!(p->perturb > 0.0)) return;
+    double d[6];
+    for (int a = 0; a < 6; a++) d[a] = sqrt(fabs(N[7 * a]));
     for (int a = 0; a < 6; a++) {
         for (int c = a; c < 6; c++) {
-            const double f = 1.0 + p->perturb * noise_at(key * 64 + (unsigned long long)(6 * a + c));
-            N[6 * a + c] *= f;
-            if (c != a) N[6 * c + a] *= f;
+            const double e = p->perturb * noise_at(key * 64 + (unsigned long long)(6 * a + c)) * d[a] * d[c];
+            N[6 * a + c] += e;
+            if (c != a) N[6 * c + a] += e;
         }
-        rhs[a] *= 1.0 + p->perturb * noise_at(key * 64 + 36 + (unsigned long long)a);
+        rhs[a] += p->perturb * noise_at(key * 64 + 36 + (unsigned long long)a) * d[a] * sqrt(fabs(E));
     }
 }
 
@@ -189,16 +204,58 @@ static void perturb_system(const or_params* p, unsigned long long key, double N[
 static int initial_normal_keyed(const double* depth, int H, int W, const or_params* p, int u0,
                                 int v0, double n[3], unsigned long long key);
 
+/* Calibration of the probe (not the method): the centred sums M and v of the
+ * regression below as single-precision arithmetic forms them, in the same two
+ * passes (means, then centred products) over points whose coordinates are
+ * taken relative to the centre pixel's point and rounded to single
+ * precision, every term and every running sum rounded to single precision. */
+static void regression_sums_f32(const double* depth, int H, int W, const or_params* p, int u0, int v0,
+                                double* m00, double* m01, double* m11, double* v0s, double* v1s) {
+    const int rn = p->rn;
+    double P0[3], P[3];
+    or_backproject(p, u0, v0, depth[(size_t)v0 * W + u0], P0);
+    float q[3], sq[3] = {0.0f, 0.0f, 0.0f}, acc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    int cnt = 0;
+    for (int pass = 0; pass < 2; pass++) {
+        const float mean[3] = {sq[0] / (float)(cnt > 0 ? cnt : 1), sq[1] / (float)(cnt > 0 ? cnt : 1),
+                               sq[2] / (float)(cnt > 0 ? cnt : 1)};
+        for (int v = v0 - rn; v <= v0 + rn; v++)
+            for (int u = u0 - rn; u <= u0 + rn; u++) {
+                if (u < 0 || v < 0 || u >= W || v >= H) continue;
+                const double z = depth[(size_t)v * W + u];
+                if (!range_valid(z)) continue;
+                or_backproject(p, u, v, z, P);
+                for (int c = 0; c < 3; c++) q[c] = (float)(P[c] - P0[c]);
+                if (pass == 0) {
+                    for (int c = 0; c < 3; c++) sq[c] = sq[c] + q[c];
+                    cnt++;
+                } else {
+                    const float dx = q[0] - mean[0], dy = q[1] - mean[1], dz = q[2] - mean[2];
+                    const float t[5] = {dx * dx, dx * dy, dy * dy, dx * dz, dy * dz};
+                    for (int c = 0; c < 5; c++) acc[c] = acc[c] + t[c];
+                }
+            }
+    }
+    *m00 = acc[0]; *m01 = acc[1]; *m11 = acc[2]; *v0s = acc[3]; *v1s = acc[4];
+}
+
 OR_EXPORT int or_initial_normal(const double* depth, int H, int W, const or_params* p, int u0,
                                 int v0, double n[3]) {
     return initial_normal_keyed(depth, H, W, p, u0, v0, n, p->perturb_seed);
 }
 
-static int initial_normal_keyed(const double* depth, int H, int W, const or_params* p, int u0,
-                                int v0, double n[3], unsigned long long key) {
+/* The centred sums of the regression over the valid points of the
+ * (2 rn + 1)^2 patch around (u0, v0):
+ *   sums = (M00, M01, M11, v0, v1, S_zz), M = sum (x-mx, y-my)(x-mx, y-my)^T,
+ *   v = sum (x-mx, y-my)(z-mz), S_zz = sum (z-mz)^2 (the probe's scale of v);
+ * single precision when p->f32_sums.  Returns the count of valid points (the
+ * sums are left 0 below 3). */
+static int regression_sums(const double* depth, int H, int W, const or_params* p, int u0, int v0,
+                           double sums[6]) {
     const int rn = p->rn;
     double P[3], sx = 0.0, sy = 0.0, sz = 0.0;
     int cnt = 0;
+    for (int i = 0; i < 6; i++) sums[i] = 0.0;
     for (int v = v0 - rn; v <= v0 + rn; v++)
         for (int u = u0 - rn; u <= u0 + rn; u++) {
             if (u < 0 || v < 0 || u >= W || v >= H) continue;
@@ -208,10 +265,9 @@ static int initial_normal_keyed(const double* depth, int H, int W, const or_para
             sx += P[0]; sy += P[1]; sz += P[2];
             cnt++;
         }
-    if (cnt < 3) return OR_BAD_NORMAL;
+    if (cnt < 3) return cnt;
     const double mx = sx / cnt, my = sy / cnt, mz = sz / cnt;
-    /* M = sum (x-mx, y-my)(x-mx, y-my)^T ;  v = sum (x-mx, y-my)(z-mz) */
-    double m00 = 0.0, m01 = 0.0, m11 = 0.0, v0s = 0.0, v1s = 0.0;
+    double m00 = 0.0, m01 = 0.0, m11 = 0.0, v0s = 0.0, v1s = 0.0, szz = 0.0;
     for (int v = v0 - rn; v <= v0 + rn; v++)
         for (int u = u0 - rn; u <= u0 + rn; u++) {
             if (u < 0 || v < 0 || u >= W || v >= H) continue;
@@ -221,13 +277,30 @@ static int initial_normal_keyed(const double* depth, int H, int W, const or_para
             const double dx = P[0] - mx, dy = P[1] - my, dz = P[2] - mz;
             m00 += dx * dx; m01 += dx * dy; m11 += dy * dy;
             v0s += dx * dz; v1s += dy * dz;
+            szz += dz * dz;
         }
-    if (p->perturb > 0.0) {
-        m00 *= 1.0 + p->perturb * noise_at(key * 64 + 50);
-        m01 *= 1.0 + p->perturb * noise_at(key * 64 + 51);
-        m11 *= 1.0 + p->perturb * noise_at(key * 64 + 52);
-        v0s *= 1.0 + p->perturb * noise_at(key * 64 + 53);
-        v1s *= 1.0 + p->perturb * noise_at(key * 64 + 54);
+    if (p->f32_sums) regression_sums_f32(depth, H, W, p, u0, v0, &m00, &m01, &m11, &v0s, &v1s);
+    sums[0] = m00; sums[1] = m01; sums[2] = m11; sums[3] = v0s; sums[4] = v1s; sums[5] = szz;
+    return cnt;
+}
+
+OR_EXPORT int or_regression_sums(const double* depth, int H, int W, const or_params* p, int u0, int v0,
+                                 double sums[6]) {
+    return regression_sums(depth, H, W, p, u0, v0, sums);
+}
+
+static int initial_normal_keyed(const double* depth, int H, int W, const or_params* p, int u0,
+                                int v0, double n[3], unsigned long long key) {
+    double S[6];
+    if (regression_sums(depth, H, W, p, u0, v0, S) < 3) return OR_BAD_NORMAL;
+    double m00 = S[0], m01 = S[1], m11 = S[2], v0s = S[3], v1s = S[4];
+    if (p->perturb > 0.0) { /* the probe, scaled as for the normal equations */
+        const double d0 = sqrt(fabs(m00)), d1 = sqrt(fabs(m11)), dz = sqrt(fabs(S[5]));
+        m00 += p->perturb * noise_at(key * 64 + 50) * d0 * d0;
+        m01 += p->perturb * noise_at(key * 64 + 51) * d0 * d1;
+        m11 += p->perturb * noise_at(key * 64 + 52) * d1 * d1;
+        v0s += p->perturb * noise_at(key * 64 + 53) * d0 * dz;
+        v1s += p->perturb * noise_at(key * 64 + 54) * d1 * dz;
     }
     const double det = m00 * m11 - m01 * m01, tr = m00 + m11;
     if (!(det > p->det_tol * tr * tr)) return OR_BAD_NORMAL;
@@ -347,21 +420,30 @@ OR_EXPORT double or_weight(const or_params* p, double eps, double mse) {
 
 /* Solve N b = rhs for symmetric positive definite N (6x6) by Cholesky of the
  * Jacobi-scaled matrix S = D N D, D = diag(N)^-1/2 (same solution; the scaled
- * pivots decide singularity).  Returns 0, or OR_SINGULAR. */
+ * pivots decide singularity).  Returns 0, or OR_SINGULAR.  *cond becomes at
+ * least the ratio of the largest to the smallest pivot seen (infinite when a
+ * pivot is not positive). */
 static int solve6(const double N[36], const double rhs[6], double tol, double b[6],
-                  double* min_pivot) {
+                  double* min_pivot, double* cond) {
     double D[6], S[36], L[36], y[6], z[6];
     for (int i = 0; i < 6; i++) {
-        if (!(N[7 * i] > 0.0)) return OR_SINGULAR;
+        if (!(N[7 * i] > 0.0)) {
+            *cond = INFINITY;
+            return OR_SINGULAR;
+        }
         D[i] = 1.0 / sqrt(N[7 * i]);
     }
     for (int i = 0; i < 6; i++)
         for (int j = 0; j < 6; j++) S[6 * i + j] = D[i] * N[6 * i + j] * D[j];
     memset(L, 0, sizeof L);
+    double pmax = 0.0;
     for (int j = 0; j < 6; j++) {
         double piv = S[7 * j];
         for (int k = 0; k < j; k++) piv -= L[6 * j + k] * L[6 * j + k];
         if (piv < *min_pivot) *min_pivot = piv;
+        if (piv > pmax) pmax = piv;
+        const double ratio = piv > 0.0 ? pmax / piv : INFINITY;
+        if (!(ratio <= *cond)) *cond = ratio;
         if (!(piv > tol)) return OR_SINGULAR;
         L[7 * j] = sqrt(piv);
         for (int i = j + 1; i < 6; i++) {
@@ -385,6 +467,35 @@ static int solve6(const double N[36], const double rhs[6], double tol, double b[
     return OR_OK;
 }
 
+/* Calibration of the probe (not the method): the normal equations of one
+ * iteration as single-precision arithmetic forms them.  Every term of every
+ * sum (w j_a j_c, w eps j_a) is rounded to single precision and added to a
+ * single-precision running sum in the plain order of the points.  The terms
+ * themselves come from the same double-precision residuals, Jacobian and
+ * weights as the method's own loop, so the result differs from it by the
+ * rounding of the sums alone (and of p', which the caller rounds). */
+static void normal_equations_f32(const or_params* p, const double* eps, const double* J, int m,
+                                 double mse, double N[36], double rhs[6], double* w_out) {
+    float n32[36], r32[6];
+    for (int a = 0; a < 36; a++) n32[a] = 0.0f;
+    for (int a = 0; a < 6; a++) r32[a] = 0.0f;
+    for (int i = 0; i < m; i++) {
+        const double wi = or_weight(p, eps[i], mse);
+        if (w_out) w_out[i] = wi;
+        const double* row = J + 6 * i;
+        for (int a = 0; a < 6; a++) {
+            for (int c = 0; c < 6; c++) {
+                const float term = (float)(row[a] * wi * row[c]);
+                n32[6 * a + c] = n32[6 * a + c] + term;
+            }
+            const float term = (float)(row[a] * wi * eps[i]);
+            r32[a] = r32[a] + term;
+        }
+    }
+    for (int a = 0; a < 36; a++) N[a] = (double)n32[a];
+    for (int a = 0; a < 6; a++) rhs[a] = (double)r32[a];
+}
+
 /* One iteration over the m p-relative points pts (m x 3): residuals and
  * Jacobian at the current state, weights, the normal equations
  * N = J^T W J, rhs = J^T W eps, b = N^-1 rhs, and the update
@@ -392,20 +503,22 @@ static int solve6(const double N[36], const double rhs[6], double tol, double b[
  * R <- Rot(-b_0, -b_1, 0) R.  Optional outputs N (36), rhs (6), b (6) and the
  * weights (m).  Returns OR_OK or OR_SINGULAR (state then unchanged). */
 static int irls_step_keyed(const double* pts, int m, const or_params* p, double R[9], double* tz,
-                           double* A, double* B, double* C, double* min_pivot, double* N_out,
-                           double* rhs_out, double* b_out, double* w_out, unsigned long long key);
+                           double* A, double* B, double* C, double* min_pivot, double* cond,
+                           double* N_out, double* rhs_out, double* b_out, double* w_out,
+                           unsigned long long key);
 
 OR_EXPORT int or_irls_step(const double* pts, int m, const or_params* p, double R[9], double* tz,
                            double* A, double* B, double* C, double* min_pivot, double* N_out,
                            double* rhs_out, double* b_out, double* w_out) {
-    return irls_step_keyed(pts, m, p, R, tz, A, B, C, min_pivot, N_out, rhs_out, b_out, w_out,
+    return irls_step_keyed(pts, m, p, R, tz, A, B, C, min_pivot, NULL, N_out, rhs_out, b_out, w_out,
                            p->perturb_seed);
 }
 
 static int irls_step_keyed(const double* pts, int m, const or_params* p, double R[9], double* tz,
-                           double* A, double* B, double* C, double* min_pivot, double* N_out,
-                           double* rhs_out, double* b_out, double* w_out, unsigned long long key) {
-    double N[36], rhs[6], b[6], mp = 1.0;
+                           double* A, double* B, double* C, double* min_pivot, double* cond,
+                           double* N_out, double* rhs_out, double* b_out, double* w_out,
+                           unsigned long long key) {
+    double N[36], rhs[6], b[6], mp = 1.0, cd = 1.0;
     double* eps = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     double* J = (double*)malloc(sizeof(double) * 6 * (size_t)(m > 0 ? m : 1));
     double mse = 0.0;
@@ -416,22 +529,30 @@ static int irls_step_keyed(const double* pts, int m, const or_params* p, double 
     mse = m > 0 ? mse / m : 0.0;
     memset(N, 0, sizeof N);
     memset(rhs, 0, sizeof rhs);
-    for (int i = 0; i < m; i++) {
-        const double w = or_weight(p, eps[i], mse);
-        if (w_out) w_out[i] = w;
-        const double* ji = J + 6 * i;
-        for (int a = 0; a < 6; a++) {
-            for (int c = 0; c < 6; c++) N[6 * a + c] += ji[a] * w * ji[c];
-            rhs[a] += ji[a] * w * eps[i];
+    if (p->f32_sums) {
+        normal_equations_f32(p, eps, J, m, mse, N, rhs, w_out);
+    } else {
+        for (int i = 0; i < m; i++) {
+            const double w = or_weight(p, eps[i], mse);
+            if (w_out) w_out[i] = w;
+            const double* ji = J + 6 * i;
+            for (int a = 0; a < 6; a++) {
+                for (int c = 0; c < 6; c++) N[6 * a + c] += ji[a] * w * ji[c];
+                rhs[a] += ji[a] * w * eps[i];
+            }
         }
     }
+    double E = 0.0; /* sum w eps^2, the probe's scale of the right-hand side */
+    if (p->perturb > 0.0)
+        for (int i = 0; i < m; i++) E += or_weight(p, eps[i], mse) * eps[i] * eps[i];
     free(eps);
     free(J);
-    perturb_system(p, key, N, rhs);
+    perturb_system(p, key, N, rhs, E);
     if (N_out) memcpy(N_out, N, sizeof N);
     if (rhs_out) memcpy(rhs_out, rhs, sizeof rhs);
-    const int st = solve6(N, rhs, p->pivot_tol, b, &mp);
+    const int st = solve6(N, rhs, p->pivot_tol, b, &mp, &cd);
     if (min_pivot && mp < *min_pivot) *min_pivot = mp;
+    if (cond && !(cd <= *cond)) *cond = cd;
     if (st != OR_OK) return st;
     if (b_out) memcpy(b_out, b, sizeof b);
     const double w[3] = {-b[0], -b[1], 0.0};
@@ -495,6 +616,7 @@ OR_EXPORT int or_fit_pixel(const double* depth, int H, int W, const or_params* p
                            or_result* res) {
     memset(res, 0, sizeof *res);
     res->min_pivot = 1.0;
+    res->cond = 1.0;
     const double z0 = depth[(size_t)v0 * W + u0];
     if (!range_valid(z0)) { fail(res, OR_INVALID_CENTRE); return res->status; }
     const unsigned long long pkey =
@@ -525,14 +647,18 @@ OR_EXPORT int or_fit_pixel(const double* depth, int H, int W, const or_params* p
             for (int c = 0; c < 3; c++)
                 pts[3 * i + c] *= 1.0 + p->perturb_points *
                                            noise_at((pkey * 1024 + 512) * 4096 + (unsigned long long)(3 * i + c));
+        if (p->f32_sums)  /* calibration: p' as a single-precision number */
+            for (int c = 0; c < 3; c++) pts[3 * i + c] = (double)(float)pts[3 * i + c];
     }
     free(uv);
-    double mp = 1.0;
+    double mp = 1.0, cd = 1.0;
     for (int t = 0; t < p->T; t++) {
         const unsigned long long key = pkey * 1024 + 1 + (unsigned long long)t;
-        if (irls_step_keyed(pts, m, p, R, &tz, &A, &B, &C, &mp, NULL, NULL, res->last_b, NULL, key) != OR_OK) {
+        if (irls_step_keyed(pts, m, p, R, &tz, &A, &B, &C, &mp, &cd, NULL, NULL, res->last_b, NULL, key) !=
+            OR_OK) {
             free(pts);
             res->min_pivot = mp;
+            res->cond = cd;
             res->iters = t;
             fail(res, OR_SINGULAR);
             return res->status;
@@ -541,6 +667,7 @@ OR_EXPORT int or_fit_pixel(const double* depth, int H, int W, const or_params* p
     }
     free(pts);
     res->min_pivot = mp;
+    res->cond = cd;
     res->A = A; res->B = B; res->C = C; res->tz = tz;
     memcpy(res->R, R, sizeof R);
     or_principal(A, B, C, &res->k1, &res->k2);
@@ -554,7 +681,8 @@ OR_EXPORT int or_fit_pixel(const double* depth, int H, int W, const or_params* p
 /* whole images                                                              */
 
 static void store(const or_result* r, size_t i, double* k1, double* k2, double* normal,
-                  int* status, double* min_pivot, double* last_b) {
+                  int* status, double* min_pivot, double* last_b, double* cond) {
+    if (cond) cond[i] = r->cond;
     if (last_b) for (int c = 0; c < 6; c++) last_b[6 * i + c] = r->last_b[c];
     if (k1) k1[i] = r->k1;
     if (k2) k2[i] = r->k2;
@@ -581,18 +709,18 @@ OR_EXPORT int or_max_threads(void) {
 }
 
 /* All pixels of a double-precision range image; outputs are H*W (normal
- * H*W*3, last_b H*W*6), any of them may be NULL.  Pixels are independent;
+ * H*W*3, last_b H*W*6, cond H*W), any of them may be NULL.  Pixels are independent;
  * nthreads > 0 sets the OpenMP thread count. */
 OR_EXPORT void or_curvature_image_f64(const double* depth, int H, int W, const or_params* p,
                                       double* k1, double* k2, double* normal, int* status,
-                                      double* min_pivot, double* last_b, int nthreads) {
+                                      double* min_pivot, double* last_b, double* cond, int nthreads) {
     set_threads(nthreads);
     const long npx = (long)H * W;
 #pragma omp parallel for schedule(dynamic, 8)
     for (long i = 0; i < npx; i++) {
         or_result r;
         or_fit_pixel(depth, H, W, p, (int)(i % W), (int)(i / W), &r);
-        store(&r, (size_t)i, k1, k2, normal, status, min_pivot, last_b);
+        store(&r, (size_t)i, k1, k2, normal, status, min_pivot, last_b, cond);
     }
 }
 
@@ -600,13 +728,13 @@ OR_EXPORT void or_curvature_image_f64(const double* depth, int H, int W, const o
 OR_EXPORT void or_curvature_pixels_f64(const double* depth, int H, int W, const or_params* p,
                                        const int* uv, int n, double* k1, double* k2,
                                        double* normal, int* status, double* min_pivot,
-                                       double* last_b, int nthreads) {
+                                       double* last_b, double* cond, int nthreads) {
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 8)
     for (int i = 0; i < n; i++) {
         or_result r;
         or_fit_pixel(depth, H, W, p, uv[2 * i], uv[2 * i + 1], &r);
-        store(&r, (size_t)i, k1, k2, normal, status, min_pivot, last_b);
+        store(&r, (size_t)i, k1, k2, normal, status, min_pivot, last_b, cond);
     }
 }
 
@@ -619,17 +747,17 @@ static double* widen(const float* d, long npx) {
 
 OR_EXPORT void or_curvature_image(const float* depth, int H, int W, const or_params* p, double* k1,
                                   double* k2, double* normal, int* status, double* min_pivot,
-                                  double* last_b, int nthreads) {
+                                  double* last_b, double* cond, int nthreads) {
     double* d = widen(depth, (long)H * W);
-    or_curvature_image_f64(d, H, W, p, k1, k2, normal, status, min_pivot, last_b, nthreads);
+    or_curvature_image_f64(d, H, W, p, k1, k2, normal, status, min_pivot, last_b, cond, nthreads);
     free(d);
 }
 
 OR_EXPORT void or_curvature_pixels(const float* depth, int H, int W, const or_params* p,
                                    const int* uv, int n, double* k1, double* k2, double* normal,
-                                   int* status, double* min_pivot, double* last_b, int nthreads) {
+                                   int* status, double* min_pivot, double* last_b, double* cond, int nthreads) {
     double* d = widen(depth, (long)H * W);
-    or_curvature_pixels_f64(d, H, W, p, uv, n, k1, k2, normal, status, min_pivot, last_b, nthreads);
+    or_curvature_pixels_f64(d, H, W, p, uv, n, k1, k2, normal, status, min_pivot, last_b, cond, nthreads);
     free(d);
 }
 

@@ -90,8 +90,15 @@ def test_validity_flip_at_the_threshold_is_allowed():
     g.k1[3] = g.k2[3] = np.nan
     rep = parity.compare(f.k1, f.k2, f.normal, ref_of(g), PIVOT_TOL)
     assert rep.ok() and rep.n_validity_mismatch_band == 1
-    g.status[3] = BAD_NORMAL              # the 2x2 degeneracy test has no pivot record
-    assert parity.compare(f.k1, f.k2, f.normal, ref_of(g), PIVOT_TOL).ok()
+    g.status[3] = BAD_NORMAL              # the 2x2 degeneracy test has no pivot record:
+    assert not parity.compare(f.k1, f.k2, f.normal, ref_of(g), PIVOT_TOL).ok()   # not excused as such
+    flips = np.zeros(6, bool)
+    flips[3] = True                       # but excused where the probe flips the oracle's validity
+    r = parity.Reference(g, np.zeros(6), 0.0, flips)
+    rep = parity.compare(f.k1, f.k2, f.normal, r, PIVOT_TOL)
+    assert rep.ok() and rep.n_validity_mismatch_band == 1
+    flips[3], flips[2] = False, True      # a flip elsewhere excuses nothing
+    assert not parity.compare(f.k1, f.k2, f.normal, r, PIVOT_TOL).ok()
     # a coarser implementation resolution widens the band
     g.status[3] = SINGULAR
     g.min_pivot[3] = 50 * PIVOT_TOL
@@ -135,3 +142,23 @@ def test_normal_field_rule():
     assert parity.compare_normals(flip, ref).ok()
     flip[0] = np.nan                              # but not where it does not
     assert not parity.compare_normals(flip, ref).ok()
+
+
+def test_condition_rule_and_excluded_pixels_are_reported():
+    """The plainer rule (condition estimate <= 1e6) and the error on the pixels
+    the probe excludes are reported, not gated."""
+    f = field(10)
+    f.cond = np.full(10, 10.0)
+    f.cond[0] = 1e7                                  # ill-conditioned by the plainer rule
+    sens = np.zeros(10)
+    sens[[1, 2]] = 5.0                               # the probe excludes pixels 1 and 2
+    k1 = f.k1.copy()
+    k1[1] += 3.0 * parity.tolerance(f.k1[1])         # out of tolerance, excluded
+    k1[2] += 0.5 * parity.tolerance(f.k1[2])
+    k1[0] += 2.0 * parity.tolerance(f.k1[0])         # out of tolerance, not excluded
+    rep = parity.compare(k1, f.k2, f.normal, parity.Reference(f, sens, 0.0), PIVOT_TOL)
+    assert not rep.ok() and rep.n_well_posed_bad == 1
+    assert rep.n_cond_well_posed == 9 and np.isclose(rep.frac_within_tol_cond, 8 / 9)
+    assert rep.n_excluded == 2 and np.isclose(rep.max_rel_excluded, 3.0)
+    assert 0.5 < rep.p999_rel_excluded <= 3.0
+    assert rep.row()["excluded"] == 2 and np.isclose(rep.row()["cond_well_posed_frac"], 0.9)
