@@ -63,6 +63,12 @@ U = 2.0 ** -24
 POINT_ULPS = 4        # relative rounding of a single-precision p' coordinate, in units of u
 PROBE_C = 0.5         # probe amplitude a = PROBE_C sqrt(N) u (calibration above)
 PROBE_SEEDS = (1, 2, 3, 4)
+# The initial normal depends on five sums, so one probe run can leave it almost
+# unmoved by chance (the angles of single runs on one pixel spread over a
+# factor 10); sixteen runs give its largest response.  The full method's answer
+# adds up hundreds of noise terms (42 entries per iteration and every
+# coordinate), whose responses vary far less from run to run.
+NORMAL_PROBE_SEEDS = tuple(range(1, 17))
 COND_LIMIT = 1e6      # the plainer rule's condition threshold
 
 
@@ -218,11 +224,12 @@ class NormalReference:
     sens: np.ndarray     # largest angle (rad) the perturbed runs moved it; inf where validity flips
 
 
-def normal_reference(depth, p, seeds=PROBE_SEEDS, nthreads=0) -> NormalReference:
+def normal_reference(depth, p, seeds=NORMAL_PROBE_SEEDS, nthreads=0) -> NormalReference:
     """Oracle initial normals plus their sensitivity: the largest angle by
     which the probe's runs (noise of amplitude PROBE_C sqrt(N) u on the
-    regression sums, N the patch points, as for the full method) and the
-    single-precision sums move each normal; inf where validity flips."""
+    regression sums, N the patch points, and of 4 u on the coordinates of
+    each patch point relative to the centre pixel's, as for the full method)
+    and the single-precision sums move each normal; inf where validity flips."""
     from . import initial_normal_image
     n0, st = initial_normal_image(depth, p, nthreads)
     npts = (2 * int(p.rn) + 1) ** 2
@@ -230,8 +237,7 @@ def normal_reference(depth, p, seeds=PROBE_SEEDS, nthreads=0) -> NormalReference
     probes = []
     for seed in seeds:
         q = copy.copy(p)
-        q.perturb = amplitude(npts)
-        q.perturb_seed = seed
+        q.perturb, q.perturb_points, q.perturb_seed = amplitude(npts), POINT_ULPS * U, seed
         probes.append(q)
     q = copy.copy(p)
     q.f32_sums = 1

@@ -179,7 +179,8 @@ static double noise_at(unsigned long long key) {
  * and v of the initial-normal regression (v with the sum of squared centred
  * heights).  So entry (a, c) moves by up to a sqrt(N_aa N_cc): relative to
  * the Jacobi-scaled matrix D N D, D = diag(N)^-1/2, that the solve factorises,
- * every entry moves by up to a (a = perturb).  Each coordinate of p' is
+ * every entry moves by up to a (a = perturb).  Each coordinate of p' (and of
+ * the regression's patch points relative to the centre pixel's point) is
  * multiplied by 1 + a' x (a' = perturb_points).  The method's output under
  * this noise tells how far rounding of that size can move it: the tests use
  * it to find the pixels whose answer is fixed at single precision. */
@@ -250,10 +251,22 @@ OR_EXPORT int or_initial_normal(const double* depth, int H, int W, const or_para
  *   v = sum (x-mx, y-my)(z-mz), S_zz = sum (z-mz)^2 (the probe's scale of v);
  * single precision when p->f32_sums.  Returns the count of valid points (the
  * sums are left 0 below 3). */
+/* The probe's noise on a patch point: its coordinates relative to the centre
+ * pixel's point P0 multiplied by 1 + a' x (a' = perturb_points), as for p' in
+ * the fitting window; keyed by the point's place in the patch. */
+static void perturb_patch_point(const or_params* p, unsigned long long key, int slot, const double P0[3],
+                                double P[3]) {
+    if (!(p->perturb_points > 0.0)) return;
+    for (int c = 0; c < 3; c++)
+        P[c] = P0[c] + (P[c] - P0[c]) *
+                           (1.0 + p->perturb_points * noise_at((key + 700) * 4096 + (unsigned long long)(3 * slot + c)));
+}
+
 static int regression_sums(const double* depth, int H, int W, const or_params* p, int u0, int v0,
-                           double sums[6]) {
-    const int rn = p->rn;
-    double P[3], sx = 0.0, sy = 0.0, sz = 0.0;
+                           double sums[6], unsigned long long key) {
+    const int rn = p->rn, side = 2 * rn + 1;
+    double P[3], P0[3], sx = 0.0, sy = 0.0, sz = 0.0;
+    or_backproject(p, u0, v0, depth[(size_t)v0 * W + u0], P0);
     int cnt = 0;
     for (int i = 0; i < 6; i++) sums[i] = 0.0;
     for (int v = v0 - rn; v <= v0 + rn; v++)
@@ -262,6 +275,7 @@ static int regression_sums(const double* depth, int H, int W, const or_params* p
             double z = depth[(size_t)v * W + u];
             if (!range_valid(z)) continue;
             or_backproject(p, u, v, z, P);
+            perturb_patch_point(p, key, (v - v0 + rn) * side + (u - u0 + rn), P0, P);
             sx += P[0]; sy += P[1]; sz += P[2];
             cnt++;
         }
@@ -274,6 +288,7 @@ static int regression_sums(const double* depth, int H, int W, const or_params* p
             double z = depth[(size_t)v * W + u];
             if (!range_valid(z)) continue;
             or_backproject(p, u, v, z, P);
+            perturb_patch_point(p, key, (v - v0 + rn) * side + (u - u0 + rn), P0, P);
             const double dx = P[0] - mx, dy = P[1] - my, dz = P[2] - mz;
             m00 += dx * dx; m01 += dx * dy; m11 += dy * dy;
             v0s += dx * dz; v1s += dy * dz;
@@ -286,13 +301,15 @@ static int regression_sums(const double* depth, int H, int W, const or_params* p
 
 OR_EXPORT int or_regression_sums(const double* depth, int H, int W, const or_params* p, int u0, int v0,
                                  double sums[6]) {
-    return regression_sums(depth, H, W, p, u0, v0, sums);
+    or_params q = *p;
+    q.perturb_points = 0.0;
+    return regression_sums(depth, H, W, &q, u0, v0, sums, 0);
 }
 
 static int initial_normal_keyed(const double* depth, int H, int W, const or_params* p, int u0,
                                 int v0, double n[3], unsigned long long key) {
     double S[6];
-    if (regression_sums(depth, H, W, p, u0, v0, S) < 3) return OR_BAD_NORMAL;
+    if (regression_sums(depth, H, W, p, u0, v0, S, key) < 3) return OR_BAD_NORMAL;
     double m00 = S[0], m01 = S[1], m11 = S[2], v0s = S[3], v1s = S[4];
     if (p->perturb > 0.0) { /* the probe, scaled as for the normal equations */
         const double d0 = sqrt(fabs(m00)), d1 = sqrt(fabs(m11)), dz = sqrt(fabs(S[5]));
