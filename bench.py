@@ -51,6 +51,8 @@ FLOP_PER_VISIT = 101  # counted FP32 operations per window point per iteration
 FLOP_PER_SOLVE = 250  # per pixel per iteration (6x6 system, update)
 FLOP_PER_NORMAL_PT = 12
 FP32_LANES_PER_SM = 128
+SERVE_REQUESTS = 20000       # the serving workload's trace (Poisson arrivals at 2000/s)
+SERVE_HALF_REQUESTS = 4000   # the trace offered at half the measured batched capacity
 METRIC = ("Mpixel/s of (k1,k2) at 640x480 r=7 vs FP32 roofline; "
           "served frames/s + p99 at <=1e-3 rel err")
 WORKLOAD = "640x480 Kinect-like synthetic scenes, window radius 7 (15x15), 5 IRLS iterations, FP32"
@@ -67,8 +69,7 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-requests", type=int, default=None,
-                    help="requests of the serving trace (default: 20000 with --report serve, "
-                         "2000 in the main run)")
+                    help="requests of the serving trace (default 20000)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs", "table2", "sweep"],
                     default=None,
@@ -127,6 +128,69 @@ def measured_hbm_gbs():
             return float(json.load(f)["hbm_gbs"])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def cpu_model():
+    """CPU model name of the host (lscpu, else /proc/cpuinfo), for the baseline's record"""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for l in out.splitlines():
+            if l.lower().startswith("model name"):
+                return l.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for l in open("/proc/cpuinfo"):
+            if l.lower().startswith(("model name", "cpu model")):
+                return l.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def alu_peak_tflops(sms, sm_mhz):
+    """FP32 issue ceiling derived from the SM count and a clock: 128 FP32 lanes
+    per SM, 2 FLOP per fused multiply-add"""
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp32_peak(pc, dev, stream, index, seconds=1.0):
+    """The measured FP32 ceiling: the library's multiply-add microbenchmark
+    (pc_fp32_peak_kernel, packed FP32x2 and scalar) timed with CUDA events on
+    its stream over about `seconds`, SM clocks sampled meanwhile."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    blocks, iters = props.multi_processor_count * 4, 8192
+    sink = torch.empty(blocks * 256, device=dev)
+    out = {"kernel": "pc_fp32_peak_kernel: 32 independent fused multiply-add chains per thread, "
+                     f"{blocks} CTAs of 256 threads, {iters} rounds"}
+    h = stream.cuda_stream
+    for packed in (1, 0):
+        st, flop = pc.pc_fp32_peak_kernel(blocks, iters, packed, sink.data_ptr(), sink.numel(), h)
+        if st != pc.PC_OK:
+            raise RuntimeError(f"pc_fp32_peak_kernel: status {st}")
+        for _ in range(20):
+            pc.pc_fp32_peak_kernel(blocks, iters, packed, sink.data_ptr(), sink.numel(), h)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = max(20, int(seconds / max(flop / 75e12, 1e-6)))
+        clk = Clocks(index)
+        clk.__enter__()
+        e0.record(stream)
+        for _ in range(n):
+            pc.pc_fp32_peak_kernel(blocks, iters, packed, sink.data_ptr(), sink.numel(), h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk.__exit__(None, None, None)
+        c = clk.summary()
+        tf = flop * n / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        key = "packed_fp32x2" if packed else "scalar"
+        out[key] = {"tflops": tf, "sm_mhz": c["sm_mhz"], "reasons": c["reasons"],
+                    "derived_peak_at_that_clock": alu_peak_tflops(props.multi_processor_count, c["sm_mhz"])
+                    if c["sm_mhz"] else None}
+    out["tflops"] = max(out["packed_fp32x2"]["tflops"], out["scalar"]["tflops"])
+    return out
 
 
 def kernel_sources_hash():
@@ -236,6 +300,7 @@ def cpu_baseline(frames_np, intr, seconds):
             fi, v0 = fi + 1, 0
     dt = time.perf_counter() - t0
     return {"value": done / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
             "sample": f"{done} pixels ({done // W} rows of 640x480 seeded scenes), "
                       f"FP64 C oracle, {dt:.1f} s"}
 
@@ -290,6 +355,7 @@ def run_reference(args, rank, world):
             "config": {"workload": WORKLOAD, "sample": "bounded row bands of frame 0 per step",
                        "ms_per_step": f"extrapolated to {args.frames} frames of {W}x{H} from the sample's rate"},
             "cpu_baseline": {"value": v, "unit": "Mpixel/s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "cpu_model": vals[0]["cpu_model"], "nproc": vals[0]["nproc"],
                              "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -402,7 +468,7 @@ def accuracy_report(args):
 BIG_SIDE = 4096   # the organised outputs' roofline case: 16.8 Mpixel, 268 MB of HBM traffic > L2
 
 
-def outputs_report(curv, depth, stream, device_time, steps):
+def outputs_report(curv, depth, stream, device_time, steps, sm_mhz):
     """Organised outputs of the same frames: pc_backproject (HBM-bound: 4 B in,
     12 B out per pixel) and pc_initial_normals, per 640x480 frame (one launch
     each, launch-latency bound) and on one 4096 x 4096 image tiled from the
@@ -430,7 +496,8 @@ def outputs_report(curv, depth, stream, device_time, steps):
     gbs = 16 * px / (ms_bbp * 1e-3) / 1e9
     normal_flop = px * (FLOP_PER_NORMAL_PT * 49 + 20)     # 7x7 patch, 2x2 solve and normalisation
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    alu_peak = alu_peak_tflops(props.multi_processor_count, sm_mhz) if sm_mhz else None
+    achieved_n0 = normal_flop / (ms_bn0 * 1e-3) / 1e12
     return {
         "backproject": {
             "ms_per_640x480_frame": ms_bp, "ms_4096x4096": ms_bbp, "mpixel_per_s_4096x4096": px / ms_bbp / 1e3,
@@ -439,20 +506,28 @@ def outputs_report(curv, depth, stream, device_time, steps):
                          "case": "one 4096x4096 image", "peak_basis": "measured HBM copy bandwidth"}},
         "initial_normals": {
             "ms_per_640x480_frame": ms_n0, "ms_4096x4096": ms_bn0, "mpixel_per_s_4096x4096": px / ms_bn0 / 1e3,
-            "roofline": {"bound": "alu", "achieved": normal_flop / (ms_bn0 * 1e-3) / 1e12, "peak": alu_peak,
-                         "unit": "TFLOP/s", "frac": normal_flop / (ms_bn0 * 1e-3) / 1e12 / alu_peak,
-                         "counted_flop_per_pixel": FLOP_PER_NORMAL_PT * 49 + 20, "case": "one 4096x4096 image"}},
+            "roofline": {"bound": "alu", "achieved": achieved_n0, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": achieved_n0 / alu_peak if alu_peak else None,
+                         "counted_flop_per_pixel": FLOP_PER_NORMAL_PT * 49 + 20, "case": "one 4096x4096 image",
+                         "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                       f"{sm_mhz or 0:.0f} MHz sampled SM clock (derived)"}},
     }
 
 
 def precision_report(args):
     """Error of each precision variant against the FP64 oracle on one seeded
     640x480 Kinect-like frame, per window radius, with its time per frame."""
+    from paper_1707_00385_gb300 import build as pcbuild
+    pcbuild.build()
+    return precision_rows((3, 7, 11), echo=True)
+
+
+def precision_rows(radii, echo=False):
+    """precision_report's rows for the given window radii (the GPU variants and
+    the FP64 oracle on frame 0 of the seeded scenes)."""
     import torch
     import oracle
     import paper_1707_00385_gb300 as pc
-    from paper_1707_00385_gb300 import build as pcbuild
-    pcbuild.build()
     s = scenes(1)[0]
     intr = s.intrinsics
     d = torch.from_numpy(s.depth).cuda()
@@ -460,7 +535,7 @@ def precision_report(args):
                 ("fp32_fp64solve", {"pivot_tol": 1e-7, "fp64_solve_cond": 1e6}, 0),
                 ("fp16_storage", {}, 1), ("bf16_storage", {}, 2)]
     rows = []
-    for r in (3, 7, 11):
+    for r in radii:
         ref = {}
         for name, kw, fmt in variants:
             piv = kw.get("pivot_tol", 1e-5)
@@ -493,7 +568,8 @@ def precision_report(args):
                          "valid_both": int(both.sum()), "validity_mismatch": int(np.sum(ok != np.isfinite(k1))),
                          "median_abs_dk": float(np.median(err)), "p99_abs_dk": float(np.quantile(err, 0.99)),
                          "frac_within_tol": float(np.mean(rel <= 1))})
-            print(json.dumps(rows[-1]), flush=True)
+            if echo:
+                print(json.dumps(rows[-1]), flush=True)
     return rows
 
 
@@ -570,7 +646,6 @@ def sweep_report(args):
     outs = [(torch.empty((H, W), device="cuda"), torch.empty((H, W), device="cuda"),
              torch.empty((H, W, 3), device="cuda")) for _ in range(F)]
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    peak = sms * FP32_LANES_PER_SM * 2 * 2070e6
     stream = torch.cuda.Stream()
     rows = []
     for r in range(1, 13):
@@ -582,17 +657,27 @@ def sweep_report(args):
                 c.batch(frames, stream=stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk = Clocks(0)
+        clk.__enter__()
         e0.record(stream)
-        with torch.cuda.stream(stream):
-            for _ in range(5):
+        reps = 0
+        while reps < 5 or time.perf_counter() - t0 < 0.6:   # long enough for several clock samples
+            if reps == 0:
+                t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
                 c.batch(frames, stream=stream)
+            reps += 1
+            if reps % 5 == 0:
+                stream.synchronize()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / 5
+        clk.__exit__(None, None, None)
+        mhz = clk.summary()["sm_mhz"]
+        ms = e0.elapsed_time(e1) / reps
         c.close()
         res = {"window_radius": r, "window": f"{2 * r + 1}x{2 * r + 1}", "ms_per_frame": ms / F,
-               "mpixel_per_s": F * H * W / ms / 1e3, "counted_tflop_per_s": flop / ms / 1e9,
-               "frac_fp32_peak": flop / ms / 1e-3 / peak}
+               "mpixel_per_s": F * H * W / ms / 1e3, "counted_tflop_per_s": flop / ms / 1e9, "sm_mhz": mhz,
+               "frac_fp32_peak": flop / ms / 1e-3 / (alu_peak_tflops(sms, mhz) * 1e12) if mhz else None}
         rows.append(res)
         print(json.dumps(res), flush=True)
     return rows
@@ -635,8 +720,17 @@ def main():
             torch.cuda.synchronize()
             return e0.elapsed_time(e1)
 
-        print(json.dumps({"outputs": outputs_report(curv, depth, stream, device_time, max(2, args.steps // 4))}),
-              flush=True)
+        clk = Clocks(0)
+        clk.__enter__()
+        out = outputs_report(curv, depth, stream, device_time, max(2, args.steps // 4), None)
+        clk.__exit__(None, None, None)
+        mhz = clk.summary()["sm_mhz"]
+        if mhz:   # the ceiling at the clock sampled while the kernels ran
+            rf = out["initial_normals"]["roofline"]
+            rf["peak"] = alu_peak_tflops(torch.cuda.get_device_properties(0).multi_processor_count, mhz)
+            rf["frac"] = rf["achieved"] / rf["peak"]
+            rf["peak_basis"] = rf["peak_basis"].replace(" 0 MHz", f" {mhz:.0f} MHz")
+        print(json.dumps({"outputs": out, "sm_mhz": mhz}), flush=True)
         curv.close()
         return
     if args.report == "serve":
@@ -755,9 +849,12 @@ def main():
         c_.close()
 
     # ---- serving: Poisson arrivals of the mixed-resolution frames, continuous
-    # batching vs one launch per frame (same frames, same trace)
-    serve_res = serve_trace(un, args.serve_requests if args.serve_requests is not None else 2000,
+    # batching vs one launch per frame (same frames, same trace): the stated
+    # 20,000-request trace, then a shorter one offered at half the batched capacity
+    serve_res = serve_trace(un, args.serve_requests if args.serve_requests is not None else SERVE_REQUESTS,
                             args.serve_rate, seed=11)
+    half_rate = 0.5 * serve_res["continuous_batching"]["frames_per_s"]
+    serve_res["half_capacity"] = serve_trace(un, SERVE_HALF_REQUESTS, half_rate, seed=12)
 
     # ---- end to end through the host-memory entry point (pinned buffers)
     hd = [torch.from_numpy(h).pin_memory() for h in host]
@@ -799,18 +896,26 @@ def main():
     e2e_pf_val = whole_job_rate(world, e2e_pf_steps * F * H * W, wall_time(step_host_frames, e2e_pf_steps)) / 1e6
 
     # ---- organised outputs (point cloud, initial-normal field)
-    outputs = outputs_report(curv, depth, stream, device_time, max(2, args.steps // 4))
+    outputs = outputs_report(curv, depth, stream, device_time, max(2, args.steps // 4), clocks.get("sm_mhz"))
 
-    # ---- roofline of the persistent kernel: counted FP32 work vs the FP32 ALU peak
+    # ---- precision variants against the FP64 oracle (one frame, radius 7)
+    precision = precision_rows((RADIUS,)) if rank == 0 else None
+
+    # ---- roofline of the persistent kernel: counted FP32 work vs the FP32 ALU
+    # ceiling, derived at the SM clock sampled during the timed region and
+    # measured by the multiply-add microbenchmark
     props = torch.cuda.get_device_properties(dev)
-    sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sm_mhz = clocks.get("sm_mhz")
+    peak = alu_peak_tflops(props.multi_processor_count, sm_mhz) if sm_mhz else None
+    measured = fp32_peak(pc, dev, stream, local)
     achieved = flop_step / (launch_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None,
             "traffic": recorded_traffic(F),
             "kernel": f"k_fit_batch<7> (fused normal + IRLS + eigen), one persistent launch over {F} 640x480 frames",
             "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                          f"{sm_max:.0f} MHz max SM clock (derived)",
+                          f"{sm_mhz or 0:.0f} MHz, the median SM clock sampled during the timed region (derived)",
+            "measured_fp32_peak": measured, "frac_of_measured": achieved / measured["tflops"],
             "launch_ms": launch_ms, "counted_flop_per_launch": flop_step}
 
     line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
@@ -831,6 +936,7 @@ def main():
             "per_frame_launches": {"value": pf_value, "unit": "Mpixel/s", "ms_per_frame": ms_pf / max(2, args.steps // 2) / F},
             "uneven_batch": uneven,
             "serve": serve_res,
+            "precision": precision,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "roofline": roof}

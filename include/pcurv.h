@@ -202,13 +202,18 @@ pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* str
  * tile counter and a frame table of at most PC_STATIC_MAX_FRAMES frames) is a
  * fixed array inside the library (about 19 KB, held on every GPU that loads
  * the library until the process exits), and the frame table is staged
- * through a fixed host array.  The paper has no counterpart; the results equal
- * pc_compute_batch bit for bit.
+ * through a fixed host array.  The paper has no counterpart.  It runs the
+ * kernel variant pc_compute_batch runs with the same ctx (the lane group that
+ * params.lanes_per_pixel forces, else one thread per pixel), so the results
+ * equal pc_compute_batch's bit for bit.
  *   - n > PC_STATIC_MAX_FRAMES is rejected with PC_ERR_INVALID_ARG (message
  *     in pc_last_error); other arguments as for pc_compute_batch.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before any
- *     stream capture.
+ *     stream capture.  This header makes no statement on capturing later
+ *     calls into a CUDA graph.
+ *   - The frame table is copied from pageable host memory inside the
+ *     library, which the next call overwrites once this one has returned.
  *   - Every call uses the same array (the counter is cleared by each call, the
  *     table overwritten), so calls that overlap on the GPU -- on different
  *     streams or from different threads -- race: keep them on one stream or
@@ -313,6 +318,21 @@ const char* pc_status_string(pc_status s);
 
 /* Message of the last failing CUDA call seen by ctx ("" if none; ctx may be NULL). */
 const char* pc_last_error(const pc_ctx* ctx);
+
+/* Measurement utility, not part of the method (the paper has no counterpart):
+ * the single-precision issue ceiling of the current GPU, against which the
+ * curvature kernels' counted FLOP/s are reported.  Enqueues on `stream` one
+ * launch of `blocks` CTAs of 256 threads; each thread runs `iters` rounds of 32
+ * independent fused multiply-adds (packed = 1: as 16 packed FP32x2
+ * instructions; packed = 0: as 32 scalar ones), all reusing the same two
+ * operand registers, and writes one float to sink[CTA * 256 + thread] so that
+ * no work is removed.  sink: caller-owned device memory of sink_len >= blocks
+ * * 256 floats, 4-byte aligned.  *flop_out (may be NULL) receives the launch's
+ * FP32 FLOP (2 per multiply-add).  PC_ERR_INVALID_ARG for bad sizes or a sink
+ * that is not device memory; PC_ERR_CUDA if the launch fails.  Time it with
+ * CUDA events on `stream`; it changes no GPU setting. */
+pc_status pc_fp32_peak_kernel(int blocks, int iters, int packed, float* sink, long long sink_len, void* stream,
+                              double* flop_out);
 
 #ifdef __cplusplus
 }

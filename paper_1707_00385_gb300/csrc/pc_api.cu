@@ -332,6 +332,10 @@ void remember_plan(pc_ctx* ctx, int H, int W, int variant) {
 
 }  // namespace
 
+namespace pcurv {
+int ctx_forced_variant(const pc_ctx* ctx) { return forced_variant(ctx); }
+}  // namespace pcurv
+
 extern "C" {
 
 void pc_params_default(pc_params* p) {

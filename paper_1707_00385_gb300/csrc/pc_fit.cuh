@@ -40,6 +40,11 @@
 //     of each other, so one instruction does the work of two and each sum is
 //     kept as a pair of partial sums, added once per iteration.  The centre
 //     point (p' = 0) contributes only to sum w and sum w eps.
+//   * single-precision rounding of a running sum grows with the number of
+//     terms already in it, so the one-thread kernels sum PC_FOLD_ROWS window
+//     rows at a time into fresh registers and fold each such partial into a
+//     running total in shared memory, for the 20 sums of J^T W J: each term
+//     then meets a sum over a few rows instead of the whole window.
 #pragma once
 #include <cfloat>
 #include <cuda_runtime.h>
@@ -57,6 +62,15 @@
 #endif
 #ifndef PC_MIN_BLOCKS
 #define PC_MIN_BLOCKS 2
+#endif
+// Window rows summed into registers between two folds of the J^T W J sums
+// into their shared-memory totals (one-thread FP32 kernels; windows of at
+// least 2 PC_FOLD_ROWS pairs of rows).  GB300, 640 x 480, r = 7, T = 5:
+// folding every row, every 2 and every 3 rows costs 4.0, 2.7 and 1.8 % of the
+// throughput; every 2 rows brings 0.934 of a Kinect-like crop's pixels within
+// the parity tolerance against 0.919 unfolded (every row: 0.935).
+#ifndef PC_FOLD_ROWS
+#define PC_FOLD_ROWS 3
 #endif
 #define PC_STR(x) #x
 #define PC_UNROLL(n) _Pragma(PC_STR(unroll n))
@@ -229,6 +243,46 @@ __device__ __forceinline__ void visit2(Moments2& m, Moments2& c, const Coef2& k,
 __device__ __forceinline__ void first_iteration_sums(Moments2& m, Moments2& c) {
     m.h00 = m.syy; m.h01 = m.sxy; m.h11 = m.sxx; m.h14 = m.h03; m.h15 = m.h04;
     c.h00 = c.syy; c.h01 = c.sxy; c.h11 = c.sxx; c.h14 = c.h03; c.h15 = c.h04;
+}
+
+// The 20 sums of J^T W J in the order of their shared-memory totals: total i
+// of the thread lives at tot[i * nt] (nt = threads of the CTA, so a warp's
+// 8-byte accesses are contiguous).  The first iteration accumulates only the
+// first 15 (first_iteration_sums fills the other five from them).
+#define PC_FOLD_FIRST(X) X(0, s0) X(1, s1) X(2, h03) X(3, h04) X(4, h05) X(5, h13) X(6, sw) X(7, sxx) \
+    X(8, sxy) X(9, syy) X(10, m40) X(11, m31) X(12, m22) X(13, m13) X(14, m04)
+#define PC_FOLD_LATER(X) X(15, h00) X(16, h01) X(17, h11) X(18, h14) X(19, h15)
+static_assert(FOLD_SUMS == 20, "PC_FOLD_FIRST and PC_FOLD_LATER list the folded sums");
+
+// total = the partial sums of the first rows; partial = 0
+template <bool FIRST>
+__device__ __forceinline__ void fold_start(Moments2& m, f32x2* tot, int nt) {
+#define PC_FOLD_ONE(i, f) \
+    tot[(i) * nt] = m.f; \
+    m.f = 0ull;
+    PC_FOLD_FIRST(PC_FOLD_ONE)
+    if (!FIRST) { PC_FOLD_LATER(PC_FOLD_ONE) }
+#undef PC_FOLD_ONE
+}
+
+// total += the partial sums of the rows since the last fold; partial = 0
+template <bool FIRST>
+__device__ __forceinline__ void fold_rows(Moments2& m, f32x2* tot, int nt) {
+#define PC_FOLD_ONE(i, f) \
+    tot[(i) * nt] = add2(tot[(i) * nt], m.f); \
+    m.f = 0ull;
+    PC_FOLD_FIRST(PC_FOLD_ONE)
+    if (!FIRST) { PC_FOLD_LATER(PC_FOLD_ONE) }
+#undef PC_FOLD_ONE
+}
+
+// partial sums of the last rows += their totals (the whole window's sums)
+template <bool FIRST>
+__device__ __forceinline__ void fold_finish(Moments2& m, const f32x2* tot, int nt) {
+#define PC_FOLD_ONE(i, f) m.f = add2(m.f, tot[(i) * nt]);
+    PC_FOLD_FIRST(PC_FOLD_ONE)
+    if (!FIRST) { PC_FOLD_LATER(PC_FOLD_ONE) }
+#undef PC_FOLD_ONE
 }
 
 // Squared scaled residuals e^2 of a pair, 0 for invalid points (rejection pre-pass).
@@ -408,13 +462,16 @@ __device__ __forceinline__ void rotate_left(float R[9], float t0, float t1) {
 // zc, cc point at the pixel's own entries of the Z and c planes (row stride SW).
 // Rows dv = -r0 .. -s pair with rows -dv; the centre row pairs du < 0 with -du.
 // RW > 0: radius RW and stride RS fixed at compile time (columns unrolled).
-template <int RW, int RS = 1, typename F>
+// row_end(k) is called after the k-th pair of rows (k = 0, 1, ...), not after
+// the centre row.
+template <int RW, int RS = 1, typename F, typename E>
 __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, int SW, int r, int s,
-                                              F&& f) {
+                                              F&& f, E&& row_end) {
     constexpr int R0 = RW > 0 ? (RW / RS) * RS : 0;  // largest sampled offset, compile-time form
     const int r0 = (r / s) * s;
     const f32x2 STEP = pack((float)s, -(float)s);
-    for (int dv = -r0; dv < 0; dv += s) {
+    int row = 0;
+    for (int dv = -r0; dv < 0; dv += s, row++) {
         const float *za = zc + dv * SW, *zb = zc - dv * SW;
         const float *ca = cc + dv * SW, *cb = cc - dv * SW;
         const f32x2 DV = pack((float)dv, -(float)dv);
@@ -435,6 +492,7 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
                 DU = add2(DU, STEP);
             }
         }
+        row_end(row);
     }
     const f32x2 DV0 = 0ull;
     f32x2 DU = pack(-(float)r0, (float)r0);
@@ -454,6 +512,11 @@ __device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, 
             DU = add2(DU, STEP);
         }
     }
+}
+
+template <int RW, int RS = 1, typename F>
+__device__ __forceinline__ void for_each_pair(const float* zc, const float* cc, int SW, int r, int s, F&& f) {
+    for_each_pair<RW, RS>(zc, cc, SW, r, s, f, [](int) {});
 }
 
 // The share of one lane of a group of G lanes that computes one pixel
@@ -609,6 +672,8 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
     constexpr bool KAHAN = (PREC & PREC_KAHAN) != 0;
     constexpr int FMT = prec_format(PREC);
     constexpr int NW = TH * G;  // warps of the CTA
+    // fold the J^T W J sums row by row (one thread per pixel, plain sums)
+    constexpr bool FOLD = G == 1 && !KAHAN;
     static_assert(G == 1 || G == 2 || G == 4 || G == 8, "lanes per pixel");
     static_assert(G == 1 || (!KAHAN && FMT == 0), "lane groups run the plain FP32 form");
     static_assert(G == 1 || RW == 0 || RS == 1, "lane groups with a compile-time window are dense");
@@ -627,6 +692,9 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
     float* tz = smem;                       // Z plane, SH x SW
     float* tcv = smem + SW * SH;            // c plane
     int* rcnt = (int*)(tcv + SW * SH);      // valid window points per (tile row, pixel column)
+    // folded totals: FOLD_SUMS pairs per thread after the planes (8-byte aligned)
+    f32x2* fold_tot = (f32x2*)(smem + ((2 * SW * SH + SH * TILE_W + 1) & ~1)) +
+                      (threadIdx.y * TILE_W + threadIdx.x);
     const int ub = tx_ * TILE_W, vb = ty_ * TH;
 
     // stage the tile + halo (Sec. 3.2, first item: the range image): warp w
@@ -794,14 +862,40 @@ __device__ __forceinline__ void fit_tile(const FrameArgs& f, const FitConfig& cf
             visit2<REJECT, KAHAN, false>(m, comp, k, za, zb, ca, cb, DU, mul2(DV, CY0), mul2(DV, CY1),
                                          mul2(DV, CY2), thr);
         };
+        // fold the J^T W J partials after every PC_FOLD_ROWS pairs of rows: the
+        // first fold starts the totals, the centre row's partial joins at the end
+        constexpr int NT = TILE_W * TH;
+        const bool folded = FOLD && r0 / s >= 2 * PC_FOLD_ROWS;
+        auto fold_first = [&](int row) {
+            if constexpr (FOLD) {
+                if (!folded || (row + 1) % PC_FOLD_ROWS != 0) return;
+                if (row + 1 == PC_FOLD_ROWS) fold_start<true>(m, fold_tot, NT);
+                else fold_rows<true>(m, fold_tot, NT);
+            }
+        };
+        auto fold_later = [&](int row) {
+            if constexpr (FOLD) {
+                if (!folded || (row + 1) % PC_FOLD_ROWS != 0) return;
+                if (row + 1 == PC_FOLD_ROWS) fold_start<false>(m, fold_tot, NT);
+                else fold_rows<false>(m, fold_tot, NT);
+            }
+        };
         if (it == 0) {
             // A = B = C = 0 here: the cheaper first-iteration form
-            if constexpr (G == 1) for_each_pair<RW, RS>(zc, cc, SW, r, s, first);
-            else for_each_pair_lanes<RW, G>(zc, cc, SW, r, s, sub, first);
+            if constexpr (G == 1) {
+                for_each_pair<RW, RS>(zc, cc, SW, r, s, first, fold_first);
+                if (folded) fold_finish<true>(m, fold_tot, NT);
+            } else {
+                for_each_pair_lanes<RW, G>(zc, cc, SW, r, s, sub, first);
+            }
             first_iteration_sums(m, comp);
         } else {
-            if constexpr (G == 1) for_each_pair<RW, RS>(zc, cc, SW, r, s, later);
-            else for_each_pair_lanes<RW, G>(zc, cc, SW, r, s, sub, later);
+            if constexpr (G == 1) {
+                for_each_pair<RW, RS>(zc, cc, SW, r, s, later, fold_later);
+                if (folded) fold_finish<false>(m, fold_tot, NT);
+            } else {
+                for_each_pair_lanes<RW, G>(zc, cc, SW, r, s, sub, later);
+            }
         }
         if constexpr (G > 1) reduce_lanes<G>(m);
 
@@ -894,16 +988,36 @@ __global__ void __launch_bounds__(TILE_W * TH * G, PC_BLOCKS_OF(PREC) * (8 / (TH
     }
 }
 
+// Dynamic shared memory of a kernel variant: planes, counts and, for the
+// one-thread FP32 kernels, the folded totals of its 32 x TH threads.
+template <int PREC, int TH, int G>
+size_t variant_smem_bytes(const FitConfig& cfg) {
+    constexpr bool FOLD = G == 1 && (PREC & PREC_KAHAN) == 0;
+    return fit_smem_bytes(cfg, TH, FOLD ? TILE_W * TH : 0);
+}
+
+// Kernels whose dynamic shared memory exceeds the default 48 KB opt in on the
+// current device (idempotent; needed before a launch or occupancy query).
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 // Tile rows ty0 .. ty1 - 1 of the frame (0 <= ty0 < ty1 <= its tile rows).
 template <int RW, int PREC, int TH, int G = 1, int RS = 1>
 cudaError_t launch_fit_rw(const FrameArgs& f, const FitConfig& cfg, cudaStream_t stream, int ty0, int ty1) {
     const dim3 block(TILE_W, TH * G);
     const dim3 grid((f.W + TILE_W - 1) / TILE_W, ty1 - ty0);
-    const size_t smem = fit_smem_bytes(cfg, TH);
-    if (cfg.reject)
+    const size_t smem = variant_smem_bytes<PREC, TH, G>(cfg);
+    cudaError_t e;
+    if (cfg.reject) {
+        if ((e = allow_smem(k_fit<RW, true, PREC, TH, G, RS>, smem)) != cudaSuccess) return e;
         k_fit<RW, true, PREC, TH, G, RS><<<grid, block, smem, stream>>>(f, cfg, ty0);
-    else
+    } else {
+        if ((e = allow_smem(k_fit<RW, false, PREC, TH, G, RS>, smem)) != cudaSuccess) return e;
         k_fit<RW, false, PREC, TH, G, RS><<<grid, block, smem, stream>>>(f, cfg, ty0);
+    }
     return cudaGetLastError();
 }
 
@@ -911,21 +1025,30 @@ template <int RW, int PREC, int TH, int G = 1, int RS = 1>
 cudaError_t launch_batch_rw(const BatchTable* table, unsigned* next_tile, int grid, const FitConfig& cfg,
                             cudaStream_t stream) {
     const dim3 block(TILE_W, TH * G);
-    const size_t smem = fit_smem_bytes(cfg, TH);
-    if (cfg.reject)
+    const size_t smem = variant_smem_bytes<PREC, TH, G>(cfg);
+    cudaError_t e;
+    if (cfg.reject) {
+        if ((e = allow_smem(k_fit_batch<RW, true, PREC, TH, G, RS>, smem)) != cudaSuccess) return e;
         k_fit_batch<RW, true, PREC, TH, G, RS><<<grid, block, smem, stream>>>(table, next_tile, cfg);
-    else
+    } else {
+        if ((e = allow_smem(k_fit_batch<RW, false, PREC, TH, G, RS>, smem)) != cudaSuccess) return e;
         k_fit_batch<RW, false, PREC, TH, G, RS><<<grid, block, smem, stream>>>(table, next_tile, cfg);
+    }
     return cudaGetLastError();
 }
 
 template <int RW, int PREC, int TH, int G = 1, int RS = 1>
 cudaError_t occupancy_rw(const FitConfig& cfg, int* blocks_per_sm) {
-    const size_t smem = fit_smem_bytes(cfg, TH);
-    return cfg.reject ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            blocks_per_sm, k_fit_batch<RW, true, PREC, TH, G, RS>, TILE_W * TH * G, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            blocks_per_sm, k_fit_batch<RW, false, PREC, TH, G, RS>, TILE_W * TH * G, smem);
+    const size_t smem = variant_smem_bytes<PREC, TH, G>(cfg);
+    cudaError_t e;
+    if (cfg.reject) {
+        if ((e = allow_smem(k_fit_batch<RW, true, PREC, TH, G, RS>, smem)) != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fit_batch<RW, true, PREC, TH, G, RS>,
+                                                             TILE_W * TH * G, smem);
+    }
+    if ((e = allow_smem(k_fit_batch<RW, false, PREC, TH, G, RS>, smem)) != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fit_batch<RW, false, PREC, TH, G, RS>,
+                                                         TILE_W * TH * G, smem);
 }
 
 // The one-lane variants (32 x 8 and 32 x 4 tiles) of radius RW sampled every

@@ -55,11 +55,17 @@ constexpr int NORMAL_RADIUS_UNROLLED = 3;
 
 inline int halo_of(const FitConfig& c) { return c.r > c.rn ? c.r : c.rn; }
 
-// Z and c planes of the tile + halo, and per-row valid counts.
-inline size_t fit_smem_bytes(const FitConfig& c, int th) {
+// Sums of J^T W J whose running totals the one-lane FP32 kernels keep in
+// shared memory, as one pair of floats per thread (fit_tile, fold_rows).
+constexpr int FOLD_SUMS = 20;
+
+// Z and c planes of the tile + halo, per-row valid counts and, for
+// fold_threads > 0, the folded totals of that many threads (8-byte aligned).
+inline size_t fit_smem_bytes(const FitConfig& c, int th, int fold_threads = 0) {
     const int h = halo_of(c);
-    return (size_t)(TILE_W + 2 * h) * (th + 2 * h) * 2 * sizeof(float) +
-           (size_t)(th + 2 * h) * TILE_W * sizeof(int);
+    const size_t planes = (size_t)(TILE_W + 2 * h) * (th + 2 * h) * 2 * sizeof(float) +
+                          (size_t)(th + 2 * h) * TILE_W * sizeof(int);
+    return (planes + 7) / 8 * 8 + (size_t)fold_threads * FOLD_SUMS * 8;
 }
 
 inline long long tiles_of(int H, int W, int th) {
@@ -150,5 +156,8 @@ namespace pcurv {
 // for pc_last_error(), for entry points defined outside pc_api.cu.
 const FitConfig& ctx_config(const pc_ctx* ctx);
 void ctx_set_error(pc_ctx* ctx, const char* msg);
+// The tile variant the context's parameters force (a lane group of
+// lanes_per_pixel, or a one-lane tile height), else -1.
+int ctx_forced_variant(const pc_ctx* ctx);
 
 }  // namespace pcurv

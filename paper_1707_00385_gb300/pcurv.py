@@ -98,6 +98,9 @@ def load() -> ctypes.CDLL:
         L.pc_status_string.restype = ctypes.c_char_p
         L.pc_last_error.argtypes = [_vp]
         L.pc_last_error.restype = ctypes.c_char_p
+        L.pc_fp32_peak_kernel.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_longlong, _vp,
+                                          ctypes.POINTER(ctypes.c_double)]
+        L.pc_fp32_peak_kernel.restype = ctypes.c_int
         for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_compute_batch",
                   "pc_compute_batch_static", "pc_pack_depth", "pc_compute_packed", "pc_autotune", "pc_destroy",
                   "pc_compute_host_batch", "pc_backproject", "pc_initial_normals"):
@@ -202,6 +205,13 @@ def pc_status_string(status: int) -> str:
 
 def pc_last_error(ctx) -> str:
     return load().pc_last_error(ctx).decode()
+
+
+def pc_fp32_peak_kernel(blocks, iters, packed, sink, sink_len, stream):
+    """Measurement utility (not the method): returns (status, FLOP of the launch)."""
+    flop = ctypes.c_double(0.0)
+    st = load().pc_fp32_peak_kernel(blocks, iters, packed, sink, sink_len, stream, ctypes.byref(flop))
+    return st, flop.value
 
 
 # ---- torch convenience wrapper ----------------------------------------------

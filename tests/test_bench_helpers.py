@@ -85,3 +85,15 @@ def test_clock_summary():
 def test_whole_job_rate_is_weak_scaling():
     assert bench.whole_job_rate(1, 1000, 2.0) == 500.0
     assert bench.whole_job_rate(4, 1000, 2.0) == 2000.0
+
+
+def test_fp32_ceiling_is_derived_from_the_given_clock():
+    import bench
+    assert abs(bench.alu_peak_tflops(152, 2070.0) - 80.54784) < 1e-9
+    assert abs(bench.alu_peak_tflops(152, 1477.0) / bench.alu_peak_tflops(152, 2070.0) - 1477 / 2070) < 1e-12
+
+
+def test_cpu_model_is_named():
+    import bench
+    m = bench.cpu_model()
+    assert isinstance(m, str) and m.strip()

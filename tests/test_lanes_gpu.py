@@ -5,6 +5,8 @@ same rule against the FP64 oracle (oracle/parity.py); a batch with a forced
 lane group equals pc_compute with it bit for bit; pixels outside the image
 store nothing; the autotuner picks among all variants."""
 
+import json
+
 import numpy as np
 import pytest
 
@@ -35,13 +37,15 @@ def scenes():
             "small": synth.crop(k, 200, 300, 37, 45)}
 
 
-# (scene, r, T, params, well-posed floor, all-pixel floor): the one-lane cases' floors
+# (scene, r, T, params, well-posed floor, all-pixel floor): about two points
+# under the values measured on a GB300 with 2 lanes (the group size that adds
+# the most single-precision rounding)
 CASES = {
-    "sphere_r3_T3": ("sphere", 3, 3, {}, 0.85, 0.9),
-    "crop_r7": ("crop", 7, 5, {}, 0.5, 0.8),
-    "crop_r11": ("crop", 11, 5, {}, 0.3, 0.8),
-    "crop_stride2": ("crop", 7, 5, {"stride": 2}, 0.5, 0.8),
-    "crop_reject": ("crop", 7, 5, {"reject": 1}, 0.5, 0.8),
+    "sphere_r3_T3": ("sphere", 3, 3, {}, 0.89, 0.92),
+    "crop_r7": ("crop", 7, 5, {}, 0.71, 0.91),
+    "crop_r11": ("crop", 11, 5, {}, 0.61, 0.86),
+    "crop_stride2": ("crop", 7, 5, {"stride": 2}, 0.83, 0.93),
+    "crop_reject": ("crop", 7, 5, {"reject": 1}, 0.80, 0.94),
 }
 _refs = {}
 
@@ -74,6 +78,7 @@ def test_lane_group_against_oracle(gpu, orc, scenes, case, lanes):
     k1, k2, n = run(gpu, s.depth, s.intrinsics, r, T, lanes_per_pixel=lanes, **params)
     rep = parity.compare(k1, k2, n, reference(orc, case, s, r, T, params), pivot_tol=PIVOT_TOL)
     print(case, lanes, rep.summary())
+    print("PARITY_ROW " + json.dumps({"case": f"lanes{lanes}:{case}", **rep.row()}))
     assert rep.nan_pattern_ok
     assert rep.n_validity_mismatch == 0, rep.summary()
     assert rep.n_well_posed_bad == 0, rep.summary()

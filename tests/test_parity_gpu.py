@@ -6,7 +6,11 @@ well-posed pixel (the oracle's own answer is fixed to a quarter of that
 tolerance under single-precision-sized perturbation); validity agrees except
 at the singularity threshold; NaN patterns of k1, k2 and the normal agree.
 Each case also has a floor on the well-posed fraction and on the fraction of
-all pixels within tolerance, so a regression cannot hide behind the rule."""
+all pixels within tolerance, each about two points under the value measured
+on a GB300, so a regression cannot hide behind the rule."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -50,6 +54,8 @@ def check(pc, orc, scene, r, T, min_well_posed, min_within, uv=None, **params):
         k1, k2, n = k1[uv[:, 1], uv[:, 0]], k2[uv[:, 1], uv[:, 0]], n[uv[:, 1], uv[:, 0]]
     rep = parity.compare(k1, k2, n, ref, pivot_tol=PIVOT_TOL)
     print(rep.summary())
+    case = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+    print("PARITY_ROW " + json.dumps({"case": case, **rep.row()}))
     assert rep.nan_pattern_ok
     assert rep.n_validity_mismatch == 0, rep.summary()
     assert rep.n_well_posed_bad == 0, rep.summary()
@@ -73,34 +79,33 @@ def crop(kinect640):
 def test_sphere_scene_64x48(gpu, orc):
     """64 x 48 sphere (r = 0.10 m at 0.80 m) in front of a plane, 1 mm noise,
     window radius 3, 3 iterations, whole image."""
-    check(gpu, orc, synth.sphere_scene(0), 3, 3, min_well_posed=0.85, min_within=0.9)
+    check(gpu, orc, synth.sphere_scene(0), 3, 3, min_well_posed=0.89, min_within=0.92)
 
 
-@pytest.mark.parametrize("r,floor", [(3, 0.5), (7, 0.5), (11, 0.3)])
-def test_kinect_crop_radii(gpu, orc, crop, r, floor):
+@pytest.mark.parametrize("r,floor,within", [(3, 0.81, 0.955), (7, 0.71, 0.91), (11, 0.61, 0.875)])
+def test_kinect_crop_radii(gpu, orc, crop, r, floor, within):
     # larger windows mix more surfaces and settle more slowly: fewer pixels
     # have an answer fixed at single precision after 5 iterations
-    check(gpu, orc, crop, r, 5, min_well_posed=floor, min_within=0.8)
+    check(gpu, orc, crop, r, 5, min_well_posed=floor, min_within=within)
 
 
 def test_kinect_crop_sparse_window(gpu, orc, crop):
     """Strided window (run-time radius path): 15 x 15 sampled every 2 pixels."""
-    check(gpu, orc, crop, 7, 5, min_well_posed=0.5, min_within=0.8, stride=2)
+    check(gpu, orc, crop, 7, 5, min_well_posed=0.83, min_within=0.925, stride=2)
 
 
 def test_kinect_crop_runtime_radius(gpu, orc, crop):
-    """Radius 15, beyond the unrolled instantiations (3 iterations: few pixels
-    have settled, so the all-pixel floor is the main guard here)."""
-    check(gpu, orc, crop, 15, 3, min_well_posed=0.03, min_within=0.75)
+    """Radius 15, beyond the unrolled instantiations, 3 iterations."""
+    check(gpu, orc, crop, 15, 3, min_well_posed=0.52, min_within=0.845)
 
 
 def test_kinect_crop_rejection(gpu, orc, crop):
     """The rejection filter of the weighting function (weight 0 above 2 MSE)."""
-    check(gpu, orc, crop, 7, 5, min_well_posed=0.5, min_within=0.8, reject=1)
+    check(gpu, orc, crop, 7, 5, min_well_posed=0.80, min_within=0.94, reject=1)
 
 
 def test_kinect_crop_other_k_and_normal_radius(gpu, orc, crop):
-    check(gpu, orc, crop, 5, 4, min_well_posed=0.5, min_within=0.8, k=4e-4, normal_radius=2)
+    check(gpu, orc, crop, 5, 4, min_well_posed=0.75, min_within=0.94, k=4e-4, normal_radius=2)
 
 
 def test_full_frame_sampled(gpu, orc, kinect640):
@@ -111,7 +116,7 @@ def test_full_frame_sampled(gpu, orc, kinect640):
     tiles = [np.stack(np.meshgrid(np.arange(u0, u0 + 32), np.arange(v0, v0 + 8)), -1).reshape(-1, 2)
              for u0, v0 in ((0, 0), (320, 240))]
     uv = np.concatenate([uv] + tiles).astype(np.int32)
-    check(gpu, orc, kinect640, 7, 5, min_well_posed=0.6, min_within=0.85, uv=uv)
+    check(gpu, orc, kinect640, 7, 5, min_well_posed=0.74, min_within=0.935, uv=uv)
 
 
 def test_tof_scene_512x424(gpu, orc):
@@ -119,13 +124,13 @@ def test_tof_scene_512x424(gpu, orc):
     s = synth.kinect_scene(3, H=424, W=512, noise="tof")
     rng = np.random.default_rng(3)
     uv = np.stack([rng.integers(0, 512, 1500), rng.integers(0, 424, 1500)], 1).astype(np.int32)
-    check(gpu, orc, s, 7, 5, min_well_posed=0.6, min_within=0.85, uv=uv)
+    check(gpu, orc, s, 7, 5, min_well_posed=0.85, min_within=0.93, uv=uv)
 
 
 def test_noise_free_scene_all_pixels_close(gpu, orc):
     """Without noise almost every pixel converges and must match."""
     s = synth.crop(synth.kinect_scene(1, noise="none", invalid_frac=0.0), 200, 200, 48, 80)
-    check(gpu, orc, s, 7, 5, min_well_posed=0.8, min_within=0.9)
+    check(gpu, orc, s, 7, 5, min_well_posed=0.98, min_within=0.98)
 
 
 def test_closed_form_paraboloid_on_gpu(gpu):
@@ -149,22 +154,27 @@ def small_crop(kinect640):
 
 
 def test_largest_window_radius(gpu, orc, small_crop):
-    """PC_MAX_RADIUS = 24 (49 x 49 window), 2 iterations."""
+    """PC_MAX_RADIUS = 24 (49 x 49 window), 2 iterations.  Parity is not
+    claimed for this window on this crop: its windows span several surfaces
+    and even 12 iterations leave most pixels unsettled, so under
+    single-precision-sized noise the oracle's own answer moves for all but
+    about 14 % of them.  The case still checks those pixels, validity and the
+    NaN patterns, and floors the fraction of all pixels within tolerance."""
     import paper_1707_00385_gb300 as pc
     r = pc.pcurv.PC_MAX_RADIUS
-    check(gpu, orc, small_crop, r, 2, min_well_posed=0.0, min_within=0.6)
+    check(gpu, orc, small_crop, r, 2, min_well_posed=0.12, min_within=0.75)
 
 
 def test_paper_sparse_37x37_window(gpu, orc, crop):
     """The paper's sparsely sampled 37 x 37 patch: radius 18 sampled every 3 pixels."""
-    check(gpu, orc, crop, 18, 5, min_well_posed=0.2, min_within=0.75, stride=3)
+    check(gpu, orc, crop, 18, 5, min_well_posed=0.74, min_within=0.88, stride=3)
 
 
 def test_most_iterations(gpu, orc, small_crop):
     """PC_MAX_ITERATIONS = 64 at radius 3: the iterations settle, so most pixels are
     fixed at single precision again."""
     import paper_1707_00385_gb300 as pc
-    check(gpu, orc, small_crop, 3, pc.pcurv.PC_MAX_ITERATIONS, min_well_posed=0.5, min_within=0.8)
+    check(gpu, orc, small_crop, 3, pc.pcurv.PC_MAX_ITERATIONS, min_well_posed=0.76, min_within=0.92)
 
 
 def test_no_iterations(gpu, orc, crop):

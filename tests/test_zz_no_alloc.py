@@ -44,21 +44,26 @@ def table(pc, frames):
     return arr
 
 
-def within_tolerance(a, b):
-    """the element tolerance of the parity tests: |dk| <= 1e-4 + 1e-4 |k|"""
-    both = np.isfinite(a) & np.isfinite(b)
-    return np.array_equal(np.isfinite(a), np.isfinite(b)) and \
-        bool(np.all(np.abs(a[both] - b[both]) <= 1e-4 + 1e-4 * np.abs(b[both])))
+def same_bits(a, b):
+    """equal element by element, NaN where the other is NaN"""
+    import torch
+    return torch.equal(torch.isnan(a), torch.isnan(b)) and torch.equal(torch.nan_to_num(a, 3.0),
+                                                                       torch.nan_to_num(b, 3.0))
 
 
-def test_no_alloc_batch_matches_batch_on_two_calls(gpu):
+@pytest.mark.parametrize("lanes", [0, 4])
+def test_no_alloc_batch_matches_batch_on_two_calls(gpu, lanes):
+    """lanes = 4 forces a lane group of 4 threads per pixel (the moment sums
+    in another order): both entry points must run that variant."""
     import torch
     sets = [
         [synth.kinect_scene(7, H=120, W=160), synth.kinect_scene(8, H=240, W=320, noise="tof"),
          synth.crop(synth.kinect_scene(9), 100, 200, 37, 53)],
         [synth.kinect_scene(10, H=480, W=640), synth.crop(synth.kinect_scene(11), 0, 0, 9, 31)],
     ]
-    st, ctx = gpu.pc_create(525.0, 525.0, 0.0, 0.0, 7, 5)
+    prm = gpu.pcurv.pc_params_default()
+    prm.lanes_per_pixel = lanes
+    st, ctx = gpu.pc_create(525.0, 525.0, 0.0, 0.0, 7, 5, prm)
     assert st == gpu.PC_OK
     try:
         for scenes in sets:                      # two calls in a row, different frames
@@ -69,10 +74,8 @@ def test_no_alloc_batch_matches_batch_on_two_calls(gpu):
             assert st == gpu.PC_OK, gpu.pc_last_error(ctx)
             torch.cuda.synchronize()
             for (_, _, a1, a2, an), (_, _, b1, b2, bn) in zip(ref, new):
-                for x, y in ((a1, b1), (a2, b2)):
-                    assert within_tolerance(y.cpu().numpy(), x.cpu().numpy())
-                assert within_tolerance(bn.cpu().numpy(), an.cpu().numpy())
-                assert torch.equal(torch.nan_to_num(a1, 3.0), torch.nan_to_num(b1, 3.0))
+                assert same_bits(a1, b1) and same_bits(a2, b2) and same_bits(an, bn)
+                assert torch.isfinite(a1).float().mean() > 0.5     # the frames were computed
     finally:
         gpu.pc_destroy(ctx)
 
