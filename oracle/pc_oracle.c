@@ -82,7 +82,8 @@ typedef struct {
     unsigned long long perturb_seed;
     int f32_sums;          /* calibration of the probe, not the method: 1 = p' rounded to single
                               precision and every sum of the normal equations and of the
-                              initial-normal regression added in single precision */
+                              initial-normal regression added in single precision; 2, 3 = the
+                              same with J^T W J from TF32 features (see normal_equations_f32) */
 } or_params;
 
 typedef struct {
@@ -484,13 +485,27 @@ static int solve6(const double N[36], const double rhs[6], double tol, double b[
     return OR_OK;
 }
 
+/* TF32 of a single-precision number (10 explicit mantissa bits, rounded to
+ * nearest with ties away from zero), as tensor cores read their operands. */
+static float to_tf32(float x) {
+    unsigned int u;
+    memcpy(&u, &x, sizeof u);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    float y;
+    memcpy(&y, &u, sizeof y);
+    return y;
+}
+
 /* Calibration of the probe (not the method): the normal equations of one
  * iteration as single-precision arithmetic forms them.  Every term of every
  * sum (w j_a j_c, w eps j_a) is rounded to single precision and added to a
  * single-precision running sum in the plain order of the points.  The terms
  * themselves come from the same double-precision residuals, Jacobian and
  * weights as the method's own loop, so the result differs from it by the
- * rounding of the sums alone (and of p', which the caller rounds). */
+ * rounding of the sums alone (and of p', which the caller rounds).
+ * f32_sums = 2 or 3 forms the terms of J^T W J as tensor cores would from
+ * the single-precision features f_a = sqrt(w) j_a: 2 = one product of their
+ * TF32 parts, 3 = TF32 parts split in two, hi hi + hi lo + lo hi. */
 static void normal_equations_f32(const or_params* p, const double* eps, const double* J, int m,
                                  double mse, double N[36], double rhs[6], double* w_out) {
     float n32[36], r32[6];
@@ -500,9 +515,17 @@ static void normal_equations_f32(const or_params* p, const double* eps, const do
         const double wi = or_weight(p, eps[i], mse);
         if (w_out) w_out[i] = wi;
         const double* row = J + 6 * i;
+        float hi[6], lo[6];
+        for (int a = 0; a < 6; a++) {
+            const float f = (float)(sqrt(wi) * row[a]);
+            hi[a] = to_tf32(f);
+            lo[a] = to_tf32(f - hi[a]);
+        }
         for (int a = 0; a < 6; a++) {
             for (int c = 0; c < 6; c++) {
-                const float term = (float)(row[a] * wi * row[c]);
+                const float term = p->f32_sums == 2   ? hi[a] * hi[c]
+                                   : p->f32_sums == 3 ? hi[a] * hi[c] + (hi[a] * lo[c] + lo[a] * hi[c])
+                                                      : (float)(row[a] * wi * row[c]);
                 n32[6 * a + c] = n32[6 * a + c] + term;
             }
             const float term = (float)(row[a] * wi * eps[i]);

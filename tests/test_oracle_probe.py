@@ -197,3 +197,23 @@ def test_probe_flags_some_but_not_all_noisy_pixels(orc, noisy):
     valid = ref.field.status == 0
     flagged = np.mean(ref.sens[valid] > 0.25)
     assert 0.0 < flagged < 0.8, flagged
+
+
+def test_tensor_core_moments_need_the_split(orc, noisy):
+    """The accuracy side of forming J^T W J on tensor cores (a design
+    question, not the method): with one TF32 product per term far fewer
+    pixels of a noisy crop stay within the parity tolerance of the FP64
+    oracle than with single-precision sums, while the three-product split
+    keeps them at the single-precision level."""
+    p = orc.params(*noisy.intrinsics, r=7, T=5)
+    f = orc.curvature_image(noisy.depth, p)
+    within = {}
+    for mode in (1, 2, 3):
+        q = copy.copy(p)
+        q.f32_sums = mode
+        g = orc.curvature_image(noisy.depth, q)
+        both = (f.status == orc.OK) & (g.status == orc.OK)
+        rel = np.maximum(np.abs(g.k1 - f.k1) / parity.tolerance(f.k1), np.abs(g.k2 - f.k2) / parity.tolerance(f.k2))
+        within[mode] = float(np.mean(rel[both] <= 1))
+    assert within[2] < within[1] - 0.1, within
+    assert abs(within[3] - within[1]) < 0.02, within
