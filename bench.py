@@ -71,14 +71,18 @@ def parse(argv=None):
     ap.add_argument("--serve-requests", type=int, default=None,
                     help="requests of the serving trace (default 20000)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs", "table2", "sweep"],
+    ap.add_argument("--fp32-peak-seconds", type=float, default=1.0,
+                    help="timed length of each form of the multiply-add microbenchmark")
+    ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs", "table2", "sweep",
+                                         "tensorcore"],
                     default=None,
                     help="instead of the benchmark line: precision = error of each precision variant "
                          "against the FP64 oracle (one 640x480 frame, radii 3, 7, 11); serve = the "
                          "serving trace and a point at half capacity; accuracy = error against "
                          "analytic ground truth; outputs = the organised outputs alone; table2 = the "
                          "paper's timing grid (3 resolutions x 9x9, 21x21, sparse 37x37 windows); sweep = "
-                         "throughput and FP32-roofline fraction for window radii 1..12 at 640x480")
+                         "throughput and FP32-roofline fraction for window radii 1..12 at 640x480; "
+                         "tensorcore = the window moments on the FP32 pipe against tensor cores")
     return ap.parse_args(argv)
 
 
@@ -683,8 +687,70 @@ def sweep_report(args):
     return rows
 
 
+def tensorcore_report(args):
+    """The window moments of one 640 x 480 frame's 5 iterations (307,200
+    windows of 15 x 15) on the FP32 pipe and on tensor cores
+    (pc_moments_probe), CUDA events over 20 launches after 3 warm-up ones, SM
+    clocks sampled; beside it the whole curvature kernel per frame."""
+    import torch
+    import paper_1707_00385_gb300 as pc
+    from paper_1707_00385_gb300 import build as pcbuild
+    pcbuild.build()
+    props = torch.cuda.get_device_properties(0)
+    sink = torch.empty(512 * props.multi_processor_count, device="cuda")
+    stream = torch.cuda.Stream()
+    h = stream.cuda_stream
+    pixels = H * W
+    res = {"pixels": pixels, "iterations": ITERS, "window": "15x15"}
+    for mode, name in ((0, "fp32_pipe"), (1, "tensor_cores_3xtf32")):
+        st, blocks = pc.pc_moments_probe(mode, pixels, ITERS, sink.data_ptr(), sink.numel(), h)
+        if st != pc.PC_OK:
+            raise RuntimeError(f"pc_moments_probe mode {mode}: status {st}")
+        for _ in range(3):
+            pc.pc_moments_probe(mode, pixels, ITERS, sink.data_ptr(), sink.numel(), h)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk = Clocks(0)
+        clk.__enter__()
+        e0.record(stream)
+        reps = 20
+        for _ in range(reps):
+            pc.pc_moments_probe(mode, pixels, ITERS, sink.data_ptr(), sink.numel(), h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk.__exit__(None, None, None)
+        res[name] = {"ms_per_frame": e0.elapsed_time(e1) / reps, "ctas": blocks, "sm_mhz": clk.summary()["sm_mhz"]}
+    res["tensor_over_fp32"] = res["tensor_cores_3xtf32"]["ms_per_frame"] / res["fp32_pipe"]["ms_per_frame"]
+    # the whole method, one persistent launch over 32 frames
+    sc = scenes(8)
+    F = 32
+    depth = [torch.from_numpy(sc[i % 8].depth).cuda() for i in range(F)]
+    outs = [(torch.empty((H, W), device="cuda"), torch.empty((H, W), device="cuda"),
+             torch.empty((H, W, 3), device="cuda")) for _ in range(F)]
+    c = pc.Curvature(*sc[0].intrinsics, window_radius=RADIUS, iterations=ITERS)
+    frames = [(depth[i], sc[i % 8].intrinsics) + outs[i] for i in range(F)]
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            c.batch(frames, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            c.batch(frames, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    c.close()
+    res["whole_method_ms_per_frame"] = e0.elapsed_time(e1) / (5 * F)
+    print(json.dumps({"tensorcore": res}), flush=True)
+    return res
+
+
 def main():
     args = parse()
+    if args.report == "tensorcore":
+        tensorcore_report(args)
+        return
     if args.report == "sweep":
         sweep_report(args)
         return
@@ -854,7 +920,8 @@ def main():
     serve_res = serve_trace(un, args.serve_requests if args.serve_requests is not None else SERVE_REQUESTS,
                             args.serve_rate, seed=11)
     half_rate = 0.5 * serve_res["continuous_batching"]["frames_per_s"]
-    serve_res["half_capacity"] = serve_trace(un, SERVE_HALF_REQUESTS, half_rate, seed=12)
+    half_n = SERVE_HALF_REQUESTS if args.serve_requests is None else max(1, args.serve_requests // 5)
+    serve_res["half_capacity"] = serve_trace(un, half_n, half_rate, seed=12)
 
     # ---- end to end through the host-memory entry point (pinned buffers)
     hd = [torch.from_numpy(h).pin_memory() for h in host]
@@ -907,7 +974,7 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = clocks.get("sm_mhz")
     peak = alu_peak_tflops(props.multi_processor_count, sm_mhz) if sm_mhz else None
-    measured = fp32_peak(pc, dev, stream, local)
+    measured = fp32_peak(pc, dev, stream, local, seconds=args.fp32_peak_seconds)
     achieved = flop_step / (launch_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if peak else None,

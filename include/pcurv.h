@@ -334,6 +334,23 @@ const char* pc_last_error(const pc_ctx* ctx);
 pc_status pc_fp32_peak_kernel(int blocks, int iters, int packed, float* sink, long long sink_len, void* stream,
                               double* flop_out);
 
+/* Design measurement, not part of the method (the paper has no counterpart):
+ * times the window moments of the re-weighted iterations (Sec. 3.2.3, Eq.
+ * iter_reweighted_update: J^T W J and J^T W eps over a 15 x 15 window) on
+ * synthetic windows, accumulated either on the FP32 pipe as the curvature
+ * kernels do (mode 0) or with tensor cores (mode 1: mma.sync m16n8k8 TF32,
+ * three products per block for single-precision accuracy, the features staged
+ * in shared memory per warp, J^T W eps on the FP32 pipe).  Both modes share
+ * the per-point work of the curvature kernels (coordinates, residual, weight,
+ * Jacobian).  Enqueues one launch on `stream` over `pixels` windows (in tiles
+ * of 32 x 8) for `iters` iterations; each thread writes one float to
+ * sink[CTA * 256 + thread] so that no work is removed.  sink: caller-owned
+ * device memory of sink_len floats, at least 512 per SM of the GPU;
+ * *blocks_out (may be NULL) receives the CTAs launched.  PC_ERR_INVALID_ARG
+ * for bad arguments or a short sink; PC_ERR_CUDA if the launch fails. */
+pc_status pc_moments_probe(int mode, int pixels, int iters, float* sink, long long sink_len, void* stream,
+                           int* blocks_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -101,6 +101,9 @@ def load() -> ctypes.CDLL:
         L.pc_fp32_peak_kernel.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_longlong, _vp,
                                           ctypes.POINTER(ctypes.c_double)]
         L.pc_fp32_peak_kernel.restype = ctypes.c_int
+        L.pc_moments_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_longlong, _vp,
+                                       ctypes.POINTER(ctypes.c_int)]
+        L.pc_moments_probe.restype = ctypes.c_int
         for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_compute_batch",
                   "pc_compute_batch_static", "pc_pack_depth", "pc_compute_packed", "pc_autotune", "pc_destroy",
                   "pc_compute_host_batch", "pc_backproject", "pc_initial_normals"):
@@ -205,6 +208,13 @@ def pc_status_string(status: int) -> str:
 
 def pc_last_error(ctx) -> str:
     return load().pc_last_error(ctx).decode()
+
+
+def pc_moments_probe(mode, pixels, iters, sink, sink_len, stream):
+    """Design measurement (not the method): returns (status, CTAs launched)."""
+    blocks = ctypes.c_int(0)
+    st = load().pc_moments_probe(mode, pixels, iters, sink, sink_len, stream, ctypes.byref(blocks))
+    return st, blocks.value
 
 
 def pc_fp32_peak_kernel(blocks, iters, packed, sink, sink_len, stream):
