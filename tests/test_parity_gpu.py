@@ -119,6 +119,29 @@ def test_full_frame_sampled(gpu, orc, kinect640):
     check(gpu, orc, kinect640, 7, 5, min_well_posed=0.74, min_within=0.935, uv=uv)
 
 
+def test_full_frame_every_pixel_batched(gpu, orc, kinect640):
+    """Every pixel of one 640 x 480 frame, r = 7, T = 5, computed by the
+    persistent batch kernel the benchmark times (pc_compute_batch)."""
+    import torch
+    c = gpu.Curvature(*kinect640.intrinsics, window_radius=7, iterations=5)
+    d = torch.from_numpy(kinect640.depth).cuda()
+    out = (torch.empty_like(d), torch.empty_like(d), torch.empty(d.shape + (3,), device="cuda"))
+    c.batch([(d, kinect640.intrinsics) + out])
+    torch.cuda.synchronize()
+    c.close()
+    from oracle import parity
+    k1, k2, n = (t.cpu().numpy() for t in out)
+    p = orc.params(*kinect640.intrinsics, r=7, T=5, pivot_tol=PIVOT_TOL)
+    rep = parity.compare(k1, k2, n, parity.reference(kinect640.depth, p), pivot_tol=PIVOT_TOL)
+    print(rep.summary())
+    case = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+    print("PARITY_ROW " + json.dumps({"case": case, **rep.row()}))
+    assert rep.ok(), rep.summary()
+    assert rep.n_well_posed >= 0.72 * rep.n_valid_oracle, rep.summary()     # 0.745 of the oracle's pixels
+    assert rep.frac_within_tol_all >= 0.93, rep.summary()                    # GB300: 0.940
+    assert rep.max_normal_angle_well_posed < 1e-4, rep.summary()
+
+
 def test_tof_scene_512x424(gpu, orc):
     """Time-of-flight noise model at 512 x 424 (sampled pixels)."""
     s = synth.kinect_scene(3, H=424, W=512, noise="tof")
