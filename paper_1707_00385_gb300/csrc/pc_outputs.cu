@@ -4,7 +4,7 @@
 //
 // k_backproject is a stream over the image (4 B in, 12 B out per pixel):
 // each thread converts four consecutive pixels, with 16-byte loads and stores
-// when the buffers allow.  k_initial_normals stages a 32 x TH tile plus a halo
+// when the buffers allow.  k_initial_normals stages a 32 x 32 tile plus a halo
 // of rn pixels in shared memory and runs the same regression device function
 // as the full path, so its normals equal those pc_compute starts from.
 #include <cfloat>
@@ -85,19 +85,22 @@ __global__ void __launch_bounds__(BP_THREADS, BP_BLOCKS_PER_SM)
     }
 }
 
-// One CTA per 32 x TH output tile; the Z plane of the tile plus a halo of rn
-// staged in shared memory (0 where the range is not valid, as the full path
-// stages it).  Registers are bounded for four 256-thread CTAs per SM (the
-// 7x7 patch, unrolled, would otherwise take more and leave three).
-template <int TH>
+// One CTA per 32 x (TH PPT) output tile: each thread computes PPT pixels of
+// its column, TH rows apart, so that one staging of the tile's Z plane plus a
+// halo of rn (0 where the range is not valid, as the full path stages it)
+// serves PPT times the arithmetic.  Registers are bounded for four 256-thread
+// CTAs per SM (the 7x7 patch, unrolled, would otherwise take more and leave
+// three).
+template <int TH, int PPT>
 __global__ void __launch_bounds__(TILE_W * TH, 4 * 8 / TH)
     k_initial_normals(const float* __restrict__ depth, int H, int W, Camera cam, int rn, float det_tol,
                       float* __restrict__ normal) {
     extern __shared__ float smem[];
     constexpr int NT = TILE_W * TH;
-    const int SW = TILE_W + 2 * rn, SH = TH + 2 * rn;
+    constexpr int TROWS = TH * PPT;
+    const int SW = TILE_W + 2 * rn, SH = TROWS + 2 * rn;
     float* tz = smem;
-    const int ub = blockIdx.x * TILE_W, vb = blockIdx.y * TH;
+    const int ub = blockIdx.x * TILE_W, vb = blockIdx.y * TROWS;
     const int tid = threadIdx.y * TILE_W + threadIdx.x;
     // element i = sy SW + sx, advanced by NT per step without a division
     const int dy = NT / SW, dx = NT - dy * SW;
@@ -118,26 +121,40 @@ __global__ void __launch_bounds__(TILE_W * TH, 4 * 8 / TH)
         }
     }
     __syncthreads();
-    const int u0 = ub + threadIdx.x, v0 = vb + threadIdx.y;
-    if (u0 >= W || v0 >= H) return;
-    const int cidx = (threadIdx.y + rn) * SW + threadIdx.x + rn;
-    const float Zp = tz[cidx];
-    float nx = 0.f, ny = 0.f, nz = 1.f;
-    bool ok = Zp > 0.f;
-    if (ok)
-        ok = rn == NORMAL_RADIUS_UNROLLED
-                 ? initial_normal<NORMAL_RADIUS_UNROLLED>(tz + cidx, SW, 0, (float)u0 - cam.cx, (float)v0 - cam.cy,
-                                                          Zp, cam, det_tol, nx, ny, nz)
-                 : initial_normal<0>(tz + cidx, SW, rn, (float)u0 - cam.cx, (float)v0 - cam.cy, Zp, cam, det_tol,
-                                     nx, ny, nz);
-    const size_t out = (size_t)v0 * W + u0;
-    const float q = __int_as_float(0x7fffffff);
-    normal[3 * out] = ok ? nx : q;
-    normal[3 * out + 1] = ok ? ny : q;
-    normal[3 * out + 2] = ok ? nz : q;
+    const int u0 = ub + threadIdx.x;
+    if (u0 >= W) return;
+#pragma unroll 1
+    for (int k = 0; k < PPT; k++) {
+        const int row = threadIdx.y + k * TH;
+        const int v0 = vb + row;
+        if (v0 >= H) return;
+        const int cidx = (row + rn) * SW + threadIdx.x + rn;
+        const float Zp = tz[cidx];
+        float nx = 0.f, ny = 0.f, nz = 1.f;
+        bool ok = Zp > 0.f;
+        if (ok)
+            ok = rn == NORMAL_RADIUS_UNROLLED
+                     ? initial_normal<NORMAL_RADIUS_UNROLLED>(tz + cidx, SW, 0, (float)u0 - cam.cx,
+                                                              (float)v0 - cam.cy, Zp, cam, det_tol, nx, ny, nz)
+                     : initial_normal<0>(tz + cidx, SW, rn, (float)u0 - cam.cx, (float)v0 - cam.cy, Zp, cam,
+                                         det_tol, nx, ny, nz);
+        const size_t out = (size_t)v0 * W + u0;
+        const float q = __int_as_float(0x7fffffff);
+        normal[3 * out] = ok ? nx : q;
+        normal[3 * out + 1] = ok ? ny : q;
+        normal[3 * out + 2] = ok ? nz : q;
+    }
 }
 
 constexpr int NORMAL_TH = 8;
+// Pixels per thread: 32 x 32 tiles.  GB300, one 4096 x 4096 image: 0.508 ms
+// with one pixel per thread (32 x 8 tiles), 0.464 with two, 0.442 with four
+// (same bits): the staging's global loads and barrier wait are spread over
+// more arithmetic.
+#ifndef PC_NORMAL_PPT
+#define PC_NORMAL_PPT 4
+#endif
+constexpr int NORMAL_PPT = PC_NORMAL_PPT;
 
 }  // namespace
 
@@ -156,15 +173,16 @@ cudaError_t launch_backproject(const float* depth, int H, int W, const Camera& c
 }
 
 size_t initial_normals_smem_bytes(int rn) {
-    return (size_t)(TILE_W + 2 * rn) * (NORMAL_TH + 2 * rn) * sizeof(float);
+    return (size_t)(TILE_W + 2 * rn) * (NORMAL_TH * NORMAL_PPT + 2 * rn) * sizeof(float);
 }
 
 cudaError_t launch_initial_normals(const float* depth, int H, int W, const Camera& cam, int rn, float det_tol,
                                    float* normal, cudaStream_t stream) {
+    constexpr int rows = NORMAL_TH * NORMAL_PPT;
     const dim3 block(TILE_W, NORMAL_TH);
-    const dim3 grid((W + TILE_W - 1) / TILE_W, (H + NORMAL_TH - 1) / NORMAL_TH);
-    k_initial_normals<NORMAL_TH><<<grid, block, initial_normals_smem_bytes(rn), stream>>>(depth, H, W, cam, rn,
-                                                                                       det_tol, normal);
+    const dim3 grid((W + TILE_W - 1) / TILE_W, (H + rows - 1) / rows);
+    k_initial_normals<NORMAL_TH, NORMAL_PPT>
+        <<<grid, block, initial_normals_smem_bytes(rn), stream>>>(depth, H, W, cam, rn, det_tol, normal);
     return cudaGetLastError();
 }
 
