@@ -98,8 +98,6 @@ def test_compute_stays_in_bounds(gpu, frames, r, params):
 @pytest.mark.parametrize("static", [False, True])
 def test_batches_stay_in_bounds(gpu, frames, params, static):
     import torch
-    if static and params:
-        pytest.skip("the static entry point always runs 32 x 8 tiles with one lane")
     c = ctx(gpu, next(iter(frames.values())), 7, **params)
     arr = (gpu.pc_frame * len(frames))()
     held = []
