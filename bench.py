@@ -687,6 +687,38 @@ def sweep_report(args):
     return rows
 
 
+def api_overhead(pc, curv, dev, stream, calls=500):
+    """Host time of one call of the C ABI (argument checks, tile plan, launch),
+    without the device work it enqueues: pc_compute on one 8 x 32 frame and
+    pc_compute_batch on that frame alone, called `calls` times back to back on
+    a stream (the enqueue time, measured on the host), through ctypes with the
+    pointers prepared beforehand.  500 calls stay below the launch queue's
+    depth, so the host never waits for the device."""
+    import torch
+    d = torch.ones((8, 32), device=dev)
+    k1, k2, n = torch.empty_like(d), torch.empty_like(d), torch.empty((8, 32, 3), device=dev)
+    h = stream.cuda_stream
+    fr = (pc.pc_frame * 1)()
+    fr[0] = pc.pc_frame(d.data_ptr(), 8, 32, 525.0, 525.0, 16.0, 4.0, k1.data_ptr(), k2.data_ptr(), n.data_ptr())
+    calls_of = {
+        "pc_compute_us": lambda: pc.pc_compute(curv.ctx, d.data_ptr(), 8, 32, h, k1.data_ptr(), k2.data_ptr(),
+                                               n.data_ptr()),
+        "pc_compute_batch_us": lambda: pc.pc_compute_batch(curv.ctx, fr, 1, h),
+    }
+    out = {"frame": "8x32, r = 7, T = 5", "calls": calls}
+    for name, call in calls_of.items():
+        for _ in range(50):
+            call()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(calls):
+            call()
+        t1 = time.perf_counter()
+        torch.cuda.synchronize()
+        out[name] = (t1 - t0) / calls * 1e6
+    return out
+
+
 def tensorcore_report(args):
     """The window moments of one 640 x 480 frame's 5 iterations (307,200
     windows of 15 x 15) on the FP32 pipe and on tensor cores
@@ -965,6 +997,9 @@ def main():
     # ---- organised outputs (point cloud, initial-normal field)
     outputs = outputs_report(curv, depth, stream, device_time, max(2, args.steps // 4), clocks.get("sm_mhz"))
 
+    # ---- host cost of one API call (what a per-frame caller pays beside the kernel)
+    overhead = api_overhead(pc, curv, dev, stream)
+
     # ---- precision variants against the FP64 oracle (one frame, radius 7)
     precision = precision_rows((RADIUS,)) if rank == 0 else None
 
@@ -1004,6 +1039,7 @@ def main():
             "uneven_batch": uneven,
             "serve": serve_res,
             "precision": precision,
+            "api_overhead": overhead,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "roofline": roof}
