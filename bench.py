@@ -53,6 +53,10 @@ FLOP_PER_NORMAL_PT = 12
 FP32_LANES_PER_SM = 128
 SERVE_REQUESTS = 20000       # the serving workload's trace (Poisson arrivals at 2000/s)
 SERVE_HALF_REQUESTS = 4000   # the trace offered at half the measured batched capacity
+# batches the continuous-batching server keeps on the GPU.  GB300, 3000 requests: 2 / 3 / 4 in
+# flight served 1403 / 1406 / 1390 frames/s at 2000/s offered, p99 6.57 / 5.91 / 5.56 ms at half
+# capacity (one launch per frame: 5.8-6.5 ms across the same runs)
+SERVE_INFLIGHT = 3
 METRIC = ("Mpixel/s of (k1,k2) at 640x480 r=7 vs FP32 roofline; "
           "served frames/s + p99 at <=1e-3 rel err")
 WORKLOAD = "640x480 Kinect-like synthetic scenes, window radius 7 (15x15), 5 IRLS iterations, FP32"
@@ -71,6 +75,8 @@ def parse(argv=None):
     ap.add_argument("--serve-requests", type=int, default=None,
                     help="requests of the serving trace (default 20000)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-inflight", type=int, default=SERVE_INFLIGHT,
+                    help="batches the continuous-batching server keeps on the GPU at once")
     ap.add_argument("--fp32-peak-seconds", type=float, default=1.0,
                     help="timed length of each form of the multiply-add microbenchmark")
     ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs", "table2", "sweep",
@@ -365,7 +371,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def serve_trace(scenes_, n, rate, seed, batched=True, plain=True):
+def serve_trace(scenes_, n, rate, seed, batched=True, plain=True, inflight=SERVE_INFLIGHT):
     """Serves n requests arriving as a Poisson process at `rate` per second,
     each a frame drawn uniformly from scenes_ (host, page-locked), with the
     continuous-batching server and with one launch per frame."""
@@ -379,7 +385,8 @@ def serve_trace(scenes_, n, rate, seed, batched=True, plain=True):
     budget = device_budget(0.5)
     out = {"requests": n, "offered_per_s": rate, "resolutions": [f"{w}x{h}" for h, w, _ in UNEVEN_SIZES],
            "budget_bytes": budget}
-    modes = ([("continuous_batching", GpuExecutor, dict(max_batch_frames=64, inflight=2))] if batched else []) + \
+    modes = ([("continuous_batching", GpuExecutor, dict(max_batch_frames=64, inflight=inflight))]
+             if batched else []) + \
             ([("one_launch_per_frame", PlainExecutor, dict(max_batch_frames=1, inflight=64))] if plain else [])
     # untimed start-up: a trace of the same rate (another seed) first, which
     # also fills the executor's pool of page-locked result buffers
@@ -387,7 +394,7 @@ def serve_trace(scenes_, n, rate, seed, batched=True, plain=True):
     tw = poisson_arrivals(nw, rate, seed + 1000)
     pick_w = np.random.default_rng(seed + 1000).integers(0, len(pool), nw)
     for name, Ex, kw in modes:
-        ex = Ex(RADIUS, ITERS)
+        ex = Ex(RADIUS, ITERS, slots=kw["inflight"]) if Ex is GpuExecutor else Ex(RADIUS, ITERS)
         warm = [Request(-1 - i, *pool[pick_w[i]], float(tw[i])) for i in range(nw)]
         Server(ex, budget, **kw).run(warm)
         reqs = [Request(i, *pool[pick[i]], float(t[i])) for i in range(n)]
@@ -836,10 +843,10 @@ def main():
         # measured batched capacity
         un = uneven_scenes(2)
         n = args.serve_requests if args.serve_requests is not None else 20000
-        full = serve_trace(un, n, args.serve_rate, seed=11)
-        print(json.dumps({"serve": full}), flush=True)
+        full = serve_trace(un, n, args.serve_rate, seed=11, inflight=args.serve_inflight)
+        print(json.dumps({"serve": full, "inflight": args.serve_inflight}), flush=True)
         cap = full["continuous_batching"]["frames_per_s"]
-        half = serve_trace(un, n, 0.5 * cap, seed=12)
+        half = serve_trace(un, n, 0.5 * cap, seed=12, inflight=args.serve_inflight)
         print(json.dumps({"serve_half_capacity": half}), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
@@ -950,10 +957,11 @@ def main():
     # batching vs one launch per frame (same frames, same trace): the stated
     # 20,000-request trace, then a shorter one offered at half the batched capacity
     serve_res = serve_trace(un, args.serve_requests if args.serve_requests is not None else SERVE_REQUESTS,
-                            args.serve_rate, seed=11)
+                            args.serve_rate, seed=11, inflight=args.serve_inflight)
     half_rate = 0.5 * serve_res["continuous_batching"]["frames_per_s"]
     half_n = SERVE_HALF_REQUESTS if args.serve_requests is None else max(1, args.serve_requests // 5)
-    serve_res["half_capacity"] = serve_trace(un, half_n, half_rate, seed=12)
+    serve_res["half_capacity"] = serve_trace(un, half_n, half_rate, seed=12, inflight=args.serve_inflight)
+    serve_res["inflight_batches"] = args.serve_inflight
 
     # ---- end to end through the host-memory entry point (pinned buffers)
     hd = [torch.from_numpy(h).pin_memory() for h in host]
