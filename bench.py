@@ -80,7 +80,7 @@ def parse(argv=None):
     ap.add_argument("--fp32-peak-seconds", type=float, default=1.0,
                     help="timed length of each form of the multiply-add microbenchmark")
     ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs", "table2", "sweep",
-                                         "tensorcore"],
+                                         "tensorcore", "fp32peak"],
                     default=None,
                     help="instead of the benchmark line: precision = error of each precision variant "
                          "against the FP64 oracle (one 640x480 frame, radii 3, 7, 11); serve = the "
@@ -88,7 +88,8 @@ def parse(argv=None):
                          "analytic ground truth; outputs = the organised outputs alone; table2 = the "
                          "paper's timing grid (3 resolutions x 9x9, 21x21, sparse 37x37 windows); sweep = "
                          "throughput and FP32-roofline fraction for window radii 1..12 at 640x480; "
-                         "tensorcore = the window moments on the FP32 pipe against tensor cores")
+                         "tensorcore = the window moments on the FP32 pipe against tensor cores; "
+                         "fp32peak = the multiply-add microbenchmark alone")
     return ap.parse_args(argv)
 
 
@@ -787,6 +788,14 @@ def tensorcore_report(args):
 
 def main():
     args = parse()
+    if args.report == "fp32peak":
+        import torch
+        import paper_1707_00385_gb300 as pc
+        from paper_1707_00385_gb300 import build as pcbuild
+        pcbuild.build()
+        res = fp32_peak(pc, torch.device("cuda", 0), torch.cuda.Stream(), 0, seconds=max(args.fp32_peak_seconds, 1.0))
+        print(json.dumps({"fp32peak": res}), flush=True)
+        return
     if args.report == "tensorcore":
         tensorcore_report(args)
         return
