@@ -1000,8 +1000,11 @@ pc_status pc_initial_normals(pc_ctx* ctx, const float* depth, int H, int W, void
     if (!depth || !normal || !aligned4(depth) || !aligned4(normal) || !is_device_ptr(depth) ||
         !is_device_ptr(normal))
         return PC_ERR_INVALID_ARG;
-    const cudaError_t e = pcurv::launch_initial_normals(depth, H, W, ctx->cam, ctx->cfg.rn, ctx->cfg.det_tol,
-                                                        normal, (cudaStream_t)stream);
+    int sms = 0;
+    cudaError_t e = sm_count(ctx, &sms);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_initial_normals");
+    e = pcurv::launch_initial_normals(depth, H, W, ctx->cam, ctx->cfg.rn, ctx->cfg.det_tol, normal, sms,
+                                      (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_initial_normals launch");
     return PC_OK;
 }

@@ -144,7 +144,7 @@ cudaError_t launch_pack(const float* depth, int H, int W, int format, unsigned s
 cudaError_t launch_backproject(const float* depth, int H, int W, const Camera& cam, float* xyz, int sms,
                                cudaStream_t stream);
 cudaError_t launch_initial_normals(const float* depth, int H, int W, const Camera& cam, int rn, float det_tol,
-                                   float* normal, cudaStream_t stream);
+                                   float* normal, int sms, cudaStream_t stream);
 
 }  // namespace pcurv
 

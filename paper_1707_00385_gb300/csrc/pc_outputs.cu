@@ -4,7 +4,7 @@
 //
 // k_backproject is a stream over the image (4 B in, 12 B out per pixel):
 // each thread converts four consecutive pixels, with 16-byte loads and stores
-// when the buffers allow.  k_initial_normals stages a 32 x 32 tile plus a halo
+// when the buffers allow.  k_initial_normals stages a 32 x (8 PPT) tile plus a halo
 // of rn pixels in shared memory and runs the same regression device function
 // as the full path, so its normals equal those pc_compute starts from.
 #include <cfloat>
@@ -147,14 +147,7 @@ __global__ void __launch_bounds__(TILE_W * TH, 4 * 8 / TH)
 }
 
 constexpr int NORMAL_TH = 8;
-// Pixels per thread: 32 x 32 tiles.  GB300, one 4096 x 4096 image: 0.508 ms
-// with one pixel per thread (32 x 8 tiles), 0.464 with two, 0.442 with four
-// (same bits): the staging's global loads and barrier wait are spread over
-// more arithmetic.
-#ifndef PC_NORMAL_PPT
-#define PC_NORMAL_PPT 4
-#endif
-constexpr int NORMAL_PPT = PC_NORMAL_PPT;
+constexpr int NORMAL_BLOCKS_PER_SM = 4;  // the kernel's launch bound
 
 }  // namespace
 
@@ -172,18 +165,37 @@ cudaError_t launch_backproject(const float* depth, int H, int W, const Camera& c
     return cudaGetLastError();
 }
 
-size_t initial_normals_smem_bytes(int rn) {
-    return (size_t)(TILE_W + 2 * rn) * (NORMAL_TH * NORMAL_PPT + 2 * rn) * sizeof(float);
+// Pixels per thread: each thread computes PPT pixels of its column from one
+// staged 32 x (8 PPT) tile plus halo, so the tile's global loads and barrier
+// wait are spread over PPT times the arithmetic.  GB300, one 4096 x 4096 image
+// (same bits): 0.508 ms with one pixel per thread, 0.464 with two, 0.442 with
+// four, 0.430 with eight.  Taller tiles make a smaller grid, so the launch
+// takes the largest PPT that still gives at least two waves of CTAs (a 640 x
+// 480 frame keeps one pixel per thread).
+static size_t initial_normals_smem_bytes(int rn, int ppt) {
+    return (size_t)(TILE_W + 2 * rn) * (NORMAL_TH * ppt + 2 * rn) * sizeof(float);
+}
+
+template <int PPT>
+static cudaError_t launch_normals_ppt(const float* depth, int H, int W, const Camera& cam, int rn, float det_tol,
+                                      float* normal, cudaStream_t stream) {
+    constexpr int rows = NORMAL_TH * PPT;
+    const dim3 block(TILE_W, NORMAL_TH);
+    const dim3 grid((W + TILE_W - 1) / TILE_W, (H + rows - 1) / rows);
+    k_initial_normals<NORMAL_TH, PPT>
+        <<<grid, block, initial_normals_smem_bytes(rn, PPT), stream>>>(depth, H, W, cam, rn, det_tol, normal);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_initial_normals(const float* depth, int H, int W, const Camera& cam, int rn, float det_tol,
-                                   float* normal, cudaStream_t stream) {
-    constexpr int rows = NORMAL_TH * NORMAL_PPT;
-    const dim3 block(TILE_W, NORMAL_TH);
-    const dim3 grid((W + TILE_W - 1) / TILE_W, (H + rows - 1) / rows);
-    k_initial_normals<NORMAL_TH, NORMAL_PPT>
-        <<<grid, block, initial_normals_smem_bytes(rn), stream>>>(depth, H, W, cam, rn, det_tol, normal);
-    return cudaGetLastError();
+                                   float* normal, int sms, cudaStream_t stream) {
+    const long long wave = 2LL * NORMAL_BLOCKS_PER_SM * (sms > 0 ? sms : 152);
+    const long long cols = (W + TILE_W - 1) / TILE_W;
+    auto tiles = [&](int ppt) { return cols * ((H + NORMAL_TH * ppt - 1) / (NORMAL_TH * ppt)); };
+    if (tiles(8) >= wave) return launch_normals_ppt<8>(depth, H, W, cam, rn, det_tol, normal, stream);
+    if (tiles(4) >= wave) return launch_normals_ppt<4>(depth, H, W, cam, rn, det_tol, normal, stream);
+    if (tiles(2) >= wave) return launch_normals_ppt<2>(depth, H, W, cam, rn, det_tol, normal, stream);
+    return launch_normals_ppt<1>(depth, H, W, cam, rn, det_tol, normal, stream);
 }
 
 }  // namespace pcurv
