@@ -142,6 +142,26 @@ def test_initial_normals_are_where_the_iterations_start(gpu, scene):
     assert np.all(cnt[extra] < 6)
 
 
+@pytest.mark.parametrize("H,W", [(720, 1280), (1200, 1600), (1600, 2560)])
+def test_initial_normals_every_tile_height(gpu, H, W):
+    """Larger images take taller tiles (two, four, eight pixels per thread on
+    a 152-SM GPU): the field keeps the same bits as the normals pc_compute
+    starts from (T = 0), which the oracle checks."""
+    import torch
+    s = synth.kinect_scene(21, H=H, W=W)
+    d = holes(s.depth, 13)
+    n0 = initial_normals(gpu, d, s.intrinsics)
+    c = gpu.Curvature(*s.intrinsics, window_radius=3, iterations=0)
+    _, _, n = c(torch.from_numpy(d).cuda())
+    torch.cuda.synchronize()
+    c.close()
+    n = n.cpu().numpy()
+    fin = np.isfinite(n).all(-1)
+    assert fin.mean() > 0.9
+    assert np.array_equal(n[fin], n0[fin])
+    assert np.isnan(n0).all(-1).sum() + np.isfinite(n0).all(-1).sum() == H * W
+
+
 # ---- pipelined host-memory batch --------------------------------------------------
 
 def host_frames(scene_list, with_normal):
