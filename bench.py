@@ -695,13 +695,12 @@ def sweep_report(args):
     return rows
 
 
-def api_overhead(pc, curv, dev, stream, calls=500):
+def api_overhead(pc, curv, dev, stream, calls=300):
     """Host time of one call of the C ABI (argument checks, tile plan, launch),
     without the device work it enqueues: pc_compute on one 8 x 32 frame and
-    pc_compute_batch on that frame alone, called `calls` times back to back on
-    a stream (the enqueue time, measured on the host), through ctypes with the
-    pointers prepared beforehand.  500 calls stay below the launch queue's
-    depth, so the host never waits for the device."""
+    pc_compute_batch on that frame alone, each call made with the stream idle
+    (synchronised before it) and timed on the host; median over `calls`
+    calls, through ctypes with the pointers prepared beforehand."""
     import torch
     d = torch.ones((8, 32), device=dev)
     k1, k2, n = torch.empty_like(d), torch.empty_like(d), torch.empty((8, 32, 3), device=dev)
@@ -713,17 +712,18 @@ def api_overhead(pc, curv, dev, stream, calls=500):
                                                n.data_ptr()),
         "pc_compute_batch_us": lambda: pc.pc_compute_batch(curv.ctx, fr, 1, h),
     }
-    out = {"frame": "8x32, r = 7, T = 5", "calls": calls}
+    out = {"frame": "8x32, r = 7, T = 5", "calls": calls, "timing": "median host time of one call, stream idle"}
     for name, call in calls_of.items():
-        for _ in range(50):
+        for _ in range(20):
             call()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        ts = []
         for _ in range(calls):
+            stream.synchronize()
+            t0 = time.perf_counter()
             call()
-        t1 = time.perf_counter()
-        torch.cuda.synchronize()
-        out[name] = (t1 - t0) / calls * 1e6
+            ts.append(time.perf_counter() - t0)
+        stream.synchronize()
+        out[name] = statistics.median(ts) * 1e6
     return out
 
 
