@@ -48,7 +48,9 @@ smallest pivot the implementation's sums resolve, when that is larger).
 The report also gives the statistics of the plainer rule that counts every
 pixel valid in both as well-posed when the oracle's condition estimate (the
 largest ratio of the largest to the smallest scaled Cholesky pivot of one
-iteration) is at most 1e6, and the error on the pixels the probe excludes.
+iteration) is at most 1e6, and the error on the pixels the probe excludes,
+in tolerances and as a multiple of the spread of the oracle's own answers
+under the probe at that pixel.
 """
 from __future__ import annotations
 
@@ -140,6 +142,8 @@ class Report:
     n_excluded: int = 0               # valid in both, not well-posed under the probe
     max_rel_excluded: float = 0.0     # max |dk| / tol over them
     p999_rel_excluded: float = 0.0    # 99.9th percentile of |dk| / tol over them
+    p99_excluded_over_spread: float = 0.0   # |dk| over the probe's own spread (sens), 99th percentile
+    max_excluded_over_spread: float = 0.0   # and maximum, over the excluded pixels with a finite spread
 
     def ok(self) -> bool:
         return self.n_validity_mismatch == 0 and self.n_well_posed_bad == 0 and self.nan_pattern_ok
@@ -153,7 +157,8 @@ class Report:
                 f"{self.max_normal_angle_well_posed:.3g} rad; cond<=1e6: {self.n_cond_well_posed} "
                 f"({self.n_cond_well_posed / max(self.n_valid_oracle, 1):.3f}) of which within tol "
                 f"{self.frac_within_tol_cond:.4f}; excluded {self.n_excluded}: max |dk|/tol "
-                f"{self.max_rel_excluded:.3g}, p99.9 {self.p999_rel_excluded:.3g}")
+                f"{self.max_rel_excluded:.3g}, p99.9 {self.p999_rel_excluded:.3g}; over the probe's spread "
+                f"p99 {self.p99_excluded_over_spread:.3g}, max {self.max_excluded_over_spread:.3g}")
 
     def row(self) -> dict:
         """the figures of one parity case, for the committed summary"""
@@ -164,7 +169,9 @@ class Report:
                 "validity_mismatch": self.n_validity_mismatch, "validity_excused": self.n_validity_mismatch_band,
                 "cond_well_posed_frac": self.n_cond_well_posed / n, "cond_within": self.frac_within_tol_cond,
                 "excluded": self.n_excluded, "max_excluded": self.max_rel_excluded,
-                "p999_excluded": self.p999_rel_excluded, "normal_angle": self.max_normal_angle_well_posed}
+                "p999_excluded": self.p999_rel_excluded, "p99_excluded_over_spread": self.p99_excluded_over_spread,
+                "max_excluded_over_spread": self.max_excluded_over_spread,
+                "normal_angle": self.max_normal_angle_well_posed}
 
 
 def compare(k1, k2, normal, ref: Reference, pivot_tol: float, band: float = 10.0,
@@ -194,13 +201,19 @@ def compare(k1, k2, normal, ref: Reference, pivot_tol: float, band: float = 10.0
         c = np.clip(np.sum(normal[wp] * f.normal[wp], -1) /
                     (np.linalg.norm(normal[wp], axis=-1) * np.linalg.norm(f.normal[wp], axis=-1)), -1, 1)
         ang = np.arccos(c)
+    # the excluded pixels' error against the spread of the oracle's own answers
+    # under the probe (in tolerances); a validity flip has no finite spread
+    fs = ex & np.isfinite(ref.sens)
+    spread = rel[fs] / ref.sens[fs] if fs.any() else np.zeros(0)
     return Report(int(o_valid.sum()), int(both.sum()), int(np.sum(mism & ~near)), int(np.sum(mism & near)),
                   int(wp.sum()), int(np.sum(rel[wp] > 1)), float(rel[wp].max()) if wp.any() else 0.0,
                   float(np.mean(rel[both] <= 1)) if both.any() else 1.0,
                   float(ang.max()) if ang.size else 0.0, nan_ok,
                   int(cw.sum()), float(np.mean(rel[cw] <= 1)) if cw.any() else 1.0,
                   int(ex.sum()), float(rel[ex].max()) if ex.any() else 0.0,
-                  float(np.quantile(rel[ex], 0.999)) if ex.any() else 0.0)
+                  float(np.quantile(rel[ex], 0.999)) if ex.any() else 0.0,
+                  float(np.quantile(spread, 0.99)) if spread.size else 0.0,
+                  float(spread.max()) if spread.size else 0.0)
 
 
 # ---- the initial-normal field on its own (Sec. 3.2.1) --------------------------

@@ -162,3 +162,16 @@ def test_condition_rule_and_excluded_pixels_are_reported():
     assert rep.n_excluded == 2 and np.isclose(rep.max_rel_excluded, 3.0)
     assert 0.5 < rep.p999_rel_excluded <= 3.0
     assert rep.row()["excluded"] == 2 and np.isclose(rep.row()["cond_well_posed_frac"], 0.9)
+
+
+def test_excluded_error_is_reported_against_the_probe_spread():
+    f = field(4)
+    sens = np.array([0.0, 2.0, 8.0, np.inf])      # pixel 3: the probe flips validity there
+    k1 = f.k1.copy()
+    k1[1] += 6.0 * parity.tolerance(f.k1[1])       # three times its spread
+    k1[2] += 4.0 * parity.tolerance(f.k1[2])       # half its spread
+    k1[3] += 100.0 * parity.tolerance(f.k1[3])     # no finite spread: not in the ratio
+    rep = parity.compare(k1, f.k2, f.normal, parity.Reference(f, sens, 0.0), PIVOT_TOL)
+    assert rep.ok() and rep.n_excluded == 3
+    assert np.isclose(rep.max_excluded_over_spread, 3.0)
+    assert 0.5 < rep.p99_excluded_over_spread <= 3.0
