@@ -163,7 +163,9 @@ pc_status pc_pack_depth(pc_ctx* ctx, const float* depth, int H, int W, int forma
 /* pc_compute reading the packed storage of pc_pack_depth (range = base +
  * offset, in FP32).  The arithmetic after loading is that of pc_compute; the
  * storage rounding is the only difference (its error against the FP64 oracle
- * is measured, not bounded by the FP32 tolerance). */
+ * is measured, not bounded by the FP32 tolerance).  Windows of radius 3, 7
+ * and 11 (dense, plain sums) run kernels with unrolled columns, others the
+ * run-time-radius kernels; both give the same bits. */
 pc_status pc_compute_packed(pc_ctx* ctx, const unsigned short* packed, const float* tile_base,
                             int format, int H, int W, void* stream, float* k1_out, float* k2_out,
                             float* normal_out);
@@ -179,6 +181,20 @@ typedef struct pc_frame {
     float* normal;       /* device, H*W*3 floats, or NULL */
 } pc_frame;
 
+/* One frame of pc_compute_packed_batch: the packed storage of pc_pack_depth
+ * (offsets: H*W 16-bit values; bases: one float per 32 x 8 tile, row-major
+ * over ceil(H/8) x ceil(W/32) tiles), its size, intrinsics and outputs as in
+ * pc_frame. */
+typedef struct pc_packed_frame {
+    const unsigned short* packed;  /* device, H*W, 2-byte aligned */
+    const float* tile_base;        /* device, 4-byte aligned */
+    int H, W;                      /* 0 <= H, W <= PC_MAX_DIM; an empty frame is skipped */
+    float fx, fy, cx, cy;
+    float* k1;                     /* device, H*W floats */
+    float* k2;                     /* device, H*W floats */
+    float* normal;                 /* device, H*W*3 floats, or NULL */
+} pc_packed_frame;
+
 /* The method on n frames of any sizes and intrinsics (0 <= n <= PC_MAX_BATCH)
  * in one persistent launch over a flattened queue of (frame, tile) items,
  * with the window radius, iterations and parameters of ctx.  `frames` is host
@@ -193,6 +209,18 @@ typedef struct pc_frame {
  * chose a lane group for that size).  Successive batch calls on one ctx must use one stream, or synchronise in
  * between, because the device scratch is shared. */
 pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream);
+
+/* pc_compute_batch for frames held in the 16-bit range storage of
+ * pc_pack_depth, all in one format (PC_DEPTH_F16 or PC_DEPTH_BF16): n frames
+ * (0 <= n <= PC_MAX_BATCH) of any sizes and intrinsics in one persistent
+ * launch over a flattened queue of their 32 x 8 tiles, with the window radius,
+ * iterations and parameters of ctx (one thread per pixel; lanes_per_pixel and
+ * tile_height do not apply).  Results equal pc_compute_packed frame by frame,
+ * bit for bit (Sec. 3.2 per pixel; the storage is ours, see pc_pack_depth).
+ * It uses ctx's batch scratch and staging like pc_compute_batch: successive
+ * batch calls on one ctx must use one stream, or synchronise in between.
+ * Arguments are checked before anything is enqueued (PC_ERR_INVALID_ARG). */
+pc_status pc_compute_packed_batch(pc_ctx* ctx, const pc_packed_frame* frames, int n, int format, void* stream);
 
 /* pc_compute_batch for callers that cannot allocate device memory.  Some
  * host programs own every byte of device memory themselves (a framework's

@@ -237,6 +237,14 @@ const KernelOps* select_ops(const FitConfig& cfg) {
     return &table.ops[dense ? cfg.r : 0];
 }
 
+const KernelOps* select_packed_ops(const FitConfig& cfg, int format) {
+    if (!cfg.kahan && cfg.stride == 1) {
+        const KernelOps* k = format == 1 ? ops_packed_f16(cfg.r) : format == 2 ? ops_packed_bf16(cfg.r) : nullptr;
+        if (k) return k;
+    }
+    return ops_precision(cfg.kahan, format);
+}
+
 const FitConfig& ctx_config(const pc_ctx* ctx) { return ctx->cfg; }
 
 void ctx_set_error(pc_ctx* ctx, const char* msg) {
@@ -528,10 +536,12 @@ pc_status pc_compute_packed(pc_ctx* ctx, const unsigned short* packed, const flo
         return PC_ERR_INVALID_ARG;
     const pcurv::FrameArgs f{nullptr, H, W, ctx->cam, k1_out, k2_out, normal_out, packed, tile_base};
     const cudaError_t e =
-        fit_frame(pcurv::ops_precision(ctx->cfg.kahan, format), 0, f, ctx->cfg, (cudaStream_t)stream);
+        fit_frame(pcurv::select_packed_ops(ctx->cfg, format), 0, f, ctx->cfg, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pc_compute_packed launch");
     return PC_OK;
 }
+
+
 
 static void free_stage(pc_ctx* ctx) {
     cudaFree(ctx->d_depth);
@@ -803,6 +813,78 @@ static pc_status batch_on(pc_ctx* ctx, BatchScratch& b, const pc_frame* frames, 
 pc_status pc_compute_batch(pc_ctx* ctx, const pc_frame* frames, int n, void* stream) {
     const HostRange range("pc_compute_batch");
     return ctx ? batch_on(ctx, ctx->batch, frames, n, stream) : PC_ERR_INVALID_ARG;
+}
+
+// Device buffers of one packed frame: present, aligned, on the device.
+static pc_status check_packed_frame(const pc_packed_frame& f) {
+    if (!f.packed || !f.tile_base || !aligned2(f.packed) || !aligned4(f.tile_base) || !is_device_ptr(f.packed) ||
+        !is_device_ptr(f.tile_base))
+        return PC_ERR_INVALID_ARG;
+    if (!f.k1 || !f.k2 || !aligned4(f.k1) || !aligned4(f.k2) || !aligned4(f.normal) || !is_device_ptr(f.k1) ||
+        !is_device_ptr(f.k2) || (f.normal && !is_device_ptr(f.normal)))
+        return PC_ERR_INVALID_ARG;
+    return PC_OK;
+}
+
+pc_status pc_compute_packed_batch(pc_ctx* ctx, const pc_packed_frame* frames, int n, int format, void* stream) {
+    const HostRange range("pc_compute_packed_batch");
+    if (!ctx || n < 0 || n > PC_MAX_BATCH || (n > 0 && !frames) ||
+        (format != PC_DEPTH_F16 && format != PC_DEPTH_BF16))
+        return PC_ERR_INVALID_ARG;
+    long long total = 0;  // 32 x 8 tiles
+    int live = 0;
+    for (int i = 0; i < n; i++) {
+        const pc_packed_frame& fr = frames[i];
+        pc_status st = check_image(fr.H, fr.W);
+        if (st != PC_OK) return st;
+        if (fr.H == 0 || fr.W == 0) continue;
+        if (!valid_intrinsics(fr.fx, fr.fy, fr.cx, fr.cy)) return PC_ERR_INVALID_ARG;
+        if ((st = check_packed_frame(fr)) != PC_OK) return st;
+        total += pcurv::tiles_of(fr.H, fr.W, 8);
+        live++;
+    }
+    if (live == 0) return PC_OK;
+    if (total > 0x7fffffffLL) return PC_ERR_INVALID_ARG;
+    BatchScratch& b = ctx->batch;
+    pc_status st = ensure_batch(ctx, b, live);
+    if (st != PC_OK) return st;
+    const pcurv::KernelOps* ops = pcurv::select_packed_ops(ctx->cfg, format);
+    int sms = 0, per_sm = 0;
+    cudaError_t e = sm_count(ctx, &sms);
+    if (e == cudaSuccess) e = ops->occupancy[0](ctx->cfg, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "packed batch occupancy");
+    const int slot = b.next;
+    b.next ^= 1;
+    if (b.pending[slot]) {
+        // the batch before last may still be reading this staging copy
+        if ((e = cudaEventSynchronize(b.done[slot])) != cudaSuccess) return cuda_fail(ctx, e, "batch wait");
+        b.pending[slot] = false;
+    }
+    pcurv::BatchTable* t = b.h_table[slot];
+    int k = 0, begin = 0;
+    for (int i = 0; i < n; i++) {
+        const pc_packed_frame& fr = frames[i];
+        if (fr.H == 0 || fr.W == 0) continue;
+        pcurv::BatchFrame& d = t->frames[k++];
+        d.f = pcurv::FrameArgs{nullptr, fr.H, fr.W,
+                               pcurv::Camera{fr.fx, fr.fy, fr.cx, fr.cy, 1.f / fr.fx, 1.f / fr.fy},
+                               fr.k1, fr.k2, fr.normal, fr.packed, fr.tile_base};
+        d.tiles_x = (fr.W + pcurv::TILE_W - 1) / pcurv::TILE_W;
+        d.tile_begin = begin;
+        begin += d.tiles_x * ((fr.H + 7) / 8);
+    }
+    t->nframes = live;
+    t->total_tiles = begin;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int slots = sms * (per_sm > 0 ? per_sm : 1);  // one CTA per tile when the queue is shorter
+    if ((e = cudaMemcpyAsync(b.d_table, t, pcurv::batch_table_bytes(live), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned), s)) != cudaSuccess ||
+        (e = ops->batch[0](b.d_table, b.d_counter, begin < slots ? begin : slots, ctx->cfg, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "packed batch launch");
+    if ((e = cudaEventRecord(b.done[slot], s)) != cudaSuccess) return cuda_fail(ctx, e, "batch event");
+    b.pending[slot] = true;
+    return PC_OK;
 }
 
 static void release_pipe(HostPipe& p) {

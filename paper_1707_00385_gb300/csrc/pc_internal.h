@@ -131,6 +131,12 @@ const KernelOps* ops_sparse(int r, int stride);
 // Run-time-radius kernels of the precision variants: compensated sums and/or
 // 16-bit range storage (format 0 float32, 1 FP16, 2 BF16).
 const KernelOps* ops_precision(int kahan, int format);
+// 16-bit range storage with unrolled columns for window radii 3, 7 and 11
+// (plain sums), else nullptr.
+const KernelOps* ops_packed_f16(int r);
+const KernelOps* ops_packed_bf16(int r);
+// The kernels reading 16-bit storage of `format` (1 FP16, 2 BF16) under cfg.
+const KernelOps* select_packed_ops(const FitConfig& cfg, int format);
 
 // The instantiation serving cfg (dense radii 1..12 unrolled, anything else
 // run-time; compensated sums on the precision kernels), all five variants.

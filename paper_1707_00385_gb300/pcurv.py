@@ -50,6 +50,15 @@ class pc_frame(ctypes.Structure):
     ]
 
 
+class pc_packed_frame(ctypes.Structure):
+    _fields_ = [
+        ("packed", ctypes.c_void_p), ("tile_base", ctypes.c_void_p),
+        ("H", ctypes.c_int), ("W", ctypes.c_int),
+        ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+        ("k1", ctypes.c_void_p), ("k2", ctypes.c_void_p), ("normal", ctypes.c_void_p),
+    ]
+
+
 class PcError(RuntimeError):
     def __init__(self, status: int, what: str, detail: str = ""):
         self.status = status
@@ -91,6 +100,7 @@ def load() -> ctypes.CDLL:
         L.pc_compute_packed.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                         _vp, _vp, _vp]
         L.pc_compute_host_batch.argtypes = [_vp, ctypes.POINTER(pc_frame), ctypes.c_int, _vp]
+        L.pc_compute_packed_batch.argtypes = [_vp, ctypes.POINTER(pc_packed_frame), ctypes.c_int, ctypes.c_int, _vp]
         L.pc_backproject.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
         L.pc_initial_normals.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
         L.pc_destroy.argtypes = [_vp]
@@ -106,7 +116,7 @@ def load() -> ctypes.CDLL:
         L.pc_moments_probe.restype = ctypes.c_int
         for f in ("pc_create", "pc_compute", "pc_compute_host", "pc_compute_batch",
                   "pc_compute_batch_static", "pc_pack_depth", "pc_compute_packed", "pc_autotune", "pc_destroy",
-                  "pc_compute_host_batch", "pc_backproject", "pc_initial_normals"):
+                  "pc_compute_host_batch", "pc_backproject", "pc_initial_normals", "pc_compute_packed_batch"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -165,6 +175,11 @@ def pc_pack_depth(ctx, depth, H, W, fmt, stream, packed, tile_base) -> int:
 
 def pc_compute_packed(ctx, packed, tile_base, fmt, H, W, stream, k1_out, k2_out, normal_out) -> int:
     return load().pc_compute_packed(ctx, packed, tile_base, fmt, H, W, stream, k1_out, k2_out, normal_out)
+
+
+def pc_compute_packed_batch(ctx, frames, n, fmt, stream) -> int:
+    """frames: a ctypes array of pc_packed_frame (or None when n == 0)."""
+    return load().pc_compute_packed_batch(ctx, frames, n, fmt, stream)
 
 
 def pc_autotune(ctx, depth, H, W, stream, k1_out, k2_out, normal_out) -> int:
@@ -374,6 +389,19 @@ class Curvature:
         if st != PC_OK:
             raise PcError(st, "pc_compute_packed", pc_last_error(self.ctx))
         return k1, k2, normal
+
+    def batch_packed(self, frames, fmt, stream=None):
+        """pc_compute_packed_batch over a list of (packed, tile_base, (fx, fy, cx, cy),
+        k1, k2, normal) tuples of CUDA tensors (the storage of pack(), all in
+        format fmt; normal may be None); enqueues one persistent launch."""
+        arr = (pc_packed_frame * max(len(frames), 1))()
+        for i, (q, base, intr, a, b, n) in enumerate(frames):
+            H, W = q.shape
+            arr[i] = pc_packed_frame(q.data_ptr(), base.data_ptr(), H, W, *map(float, intr), a.data_ptr(),
+                                     b.data_ptr(), n.data_ptr() if n is not None else None)
+        st = pc_compute_packed_batch(self.ctx, arr if frames else None, len(frames), fmt, _stream_handle(stream))
+        if st != PC_OK:
+            raise PcError(st, "pc_compute_packed_batch", pc_last_error(self.ctx))
 
     def host_batch(self, frames, stream=None):
         """pc_compute_host_batch over a list of (depth, (fx, fy, cx, cy), k1, k2,

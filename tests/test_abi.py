@@ -62,6 +62,38 @@ def test_frame_struct_matches_header(pc):
     assert names == [f for f, _ in pc.pc_frame._fields_]
 
 
+def test_packed_frame_struct_matches_header(pc):
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct pc_packed_frame \{(.*?)\} pc_packed_frame;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.replace("const ", "").replace("unsigned ", "").strip()
+        if decl:
+            names += [n.strip().lstrip("*") for n in decl.split(None, 1)[1].split(",")]
+    names = [n.lstrip("*") for n in names]
+    assert names == [f for f, _ in pc.pc_packed_frame._fields_]
+
+
+def test_packed_batch_argument_checks_without_gpu(pc):
+    st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5)
+    try:
+        assert pc.pc_compute_packed_batch(None, None, 0, 1, None) == pc.PC_ERR_INVALID_ARG
+        assert pc.pc_compute_packed_batch(ctx, None, 0, 1, None) == pc.PC_OK
+        assert pc.pc_compute_packed_batch(ctx, None, 0, 3, None) == pc.PC_ERR_INVALID_ARG   # no such format
+        assert pc.pc_compute_packed_batch(ctx, None, 1, 1, None) == pc.PC_ERR_INVALID_ARG
+        fr = (pc.pc_packed_frame * 2)()
+        fr[0] = pc.pc_packed_frame(None, None, 0, 0, 1.0, 1.0, 0.0, 0.0, None, None, None)   # empty: skipped
+        fr[1] = pc.pc_packed_frame(None, None, 0, 8, 1.0, 1.0, 0.0, 0.0, None, None, None)
+        assert pc.pc_compute_packed_batch(ctx, fr, 2, 2, None) == pc.PC_OK
+        fr[1] = pc.pc_packed_frame(None, None, 4, 4, 1.0, 1.0, 0.0, 0.0, None, None, None)   # NULL buffers
+        assert pc.pc_compute_packed_batch(ctx, fr, 2, 2, None) == pc.PC_ERR_INVALID_ARG
+        fr[1] = pc.pc_packed_frame(None, None, -4, 4, 1.0, 1.0, 0.0, 0.0, None, None, None)
+        assert pc.pc_compute_packed_batch(ctx, fr, 2, 1, None) == pc.PC_ERR_INVALID_ARG
+    finally:
+        pc.pc_destroy(ctx)
+
+
 def test_batch_argument_checks_without_gpu(pc):
     st, ctx = pc.pc_create(525.0, 525.0, 319.5, 239.5, 7, 5)
     try:

@@ -71,12 +71,14 @@ def test_pack_rounds_each_offset_once(gpu, scene, fmt):
     c.close()
 
 
+@pytest.mark.parametrize("r", [3, 5, 7, 11])
 @pytest.mark.parametrize("fmt", [1, 2])
-def test_packed_path_equals_fp32_path_on_decoded_ranges(gpu, scene, fmt):
+def test_packed_path_equals_fp32_path_on_decoded_ranges(gpu, scene, fmt, r):
     """The arithmetic after loading is the FP32 path's: same bits on the
-    decoded ranges."""
+    decoded ranges (3, 7 and 11 have window loops unrolled for the 16-bit
+    loads, 5 takes the general one)."""
     import torch
-    c = gpu.Curvature(*scene.intrinsics, window_radius=7, iterations=5)
+    c = gpu.Curvature(*scene.intrinsics, window_radius=r, iterations=5)
     d = torch.from_numpy(scene.depth).cuda()
     packed, base = c.pack(d, fmt)
     a1, a2, an = c.compute_packed(packed, base, fmt)
@@ -86,6 +88,41 @@ def test_packed_path_equals_fp32_path_on_decoded_ranges(gpu, scene, fmt):
     torch.cuda.synchronize()
     for x, y in ((a1, b1), (a2, b2), (an, bn)):
         assert np.array_equal(x.cpu().numpy(), y.cpu().numpy(), equal_nan=True)
+    c.close()
+
+
+@pytest.mark.parametrize("r", [3, 7, 11])
+@pytest.mark.parametrize("fmt", [1, 2])
+def test_packed_batch_equals_per_frame_packed(gpu, scene, fmt, r):
+    """pc_compute_packed_batch on frames of uneven sizes and intrinsics (an
+    empty one among them, one without normals) gives pc_compute_packed's bits
+    frame by frame."""
+    import torch
+    other = synth.kinect_scene(22)
+    views = [scene, synth.crop(scene, 200, 260, 70, 100), synth.crop(other, 11, 5, 37, 53),
+             synth.crop(other, 300, 300, 9, 300), synth.crop(scene, 0, 0, 480, 33)]
+    c = gpu.Curvature(*scene.intrinsics, window_radius=r, iterations=5)
+    frames, want = [], []
+    for i, v in enumerate(views):
+        cv = gpu.Curvature(*v.intrinsics, window_radius=r, iterations=5)
+        q, base = c.pack(torch.from_numpy(v.depth).cuda(), fmt)
+        want.append([x.cpu().numpy() if x is not None else None for x in cv.compute_packed(q, base, fmt)])
+        cv.close()
+        H, W = v.depth.shape
+        outs = [torch.full((H, W), 7.0, device="cuda"), torch.full((H, W), 7.0, device="cuda"),
+                None if i == 2 else torch.full((H, W, 3), 7.0, device="cuda")]
+        frames.append((q, base, v.intrinsics, *outs))
+    empty = torch.empty((0, 16), dtype=torch.int16, device="cuda")
+    frames.insert(1, (empty, torch.empty((0, 1), device="cuda"), scene.intrinsics,
+                      torch.empty((0, 16), device="cuda"), torch.empty((0, 16), device="cuda"), None))
+    c.batch_packed(frames, fmt)
+    torch.cuda.synchronize()
+    got = [f for j, f in enumerate(frames) if j != 1]
+    for i, (f, w) in enumerate(zip(got, want)):
+        for j in range(3):
+            if f[3 + j] is None:
+                continue
+            assert np.array_equal(f[3 + j].cpu().numpy(), w[j], equal_nan=True), (i, j)
     c.close()
 
 
