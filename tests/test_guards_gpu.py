@@ -5,8 +5,8 @@ into the middle of a larger buffer whose words before and after hold a
 sentinel, and the sentinels are checked after the call -- over odd image
 shapes (1x1 up to several ragged tiles), window radii (unrolled and run-time),
 strides, rejection, every kernel variant (32x8 and 32x4 tiles, 2, 4 and 8
-lanes per pixel, compensated sums, 16-bit storage) and every entry point that
-writes device or host memory."""
+lanes per pixel, compensated sums, 16-bit storage one frame at a time and in
+a batch) and every entry point that writes device or host memory."""
 import numpy as np
 import pytest
 
@@ -157,6 +157,33 @@ def test_packed_storage_stays_in_bounds(gpu, frames, fmt):
         gpu.pc_destroy(c)
         assert packed.intact() and base.intact(), (H, W)
         assert k1.intact() and k2.intact() and n.intact(), (H, W)
+
+
+@pytest.mark.parametrize("r", [3, 5, 11])
+@pytest.mark.parametrize("fmt", [1, 2])
+def test_packed_batch_stays_in_bounds(gpu, frames, fmt, r):
+    """pc_compute_packed_batch over every shape at once (unrolled radii 3 and
+    11, run-time radius 5)."""
+    import torch
+    c = ctx(gpu, next(iter(frames.values())), r)
+    arr = (gpu.pc_packed_frame * len(frames))()
+    held = []
+    for i, ((H, W), s) in enumerate(frames.items()):
+        d = torch.from_numpy(s.depth).cuda()
+        tiles = ((W + 31) // 32) * ((H + 7) // 8)
+        packed = Guarded(H * W, dtype=torch.int16, sentinel=12345)
+        base = Guarded(tiles)
+        assert gpu.pc_pack_depth(c, d.data_ptr(), H, W, fmt, None, packed.ptr, base.ptr) == gpu.PC_OK
+        k1, k2, n = outputs(H, W)
+        held.append((packed, base, k1, k2, n))
+        arr[i] = gpu.pc_packed_frame(packed.ptr, base.ptr, H, W, *map(float, s.intrinsics), k1.ptr, k2.ptr, n.ptr)
+    assert gpu.pc_compute_packed_batch(c, arr, len(frames), fmt, None) == gpu.PC_OK
+    torch.cuda.synchronize()
+    gpu.pc_destroy(c)
+    for (packed, base, k1, k2, n), hw in zip(held, frames):
+        assert packed.intact() and base.intact(), hw
+        assert k1.intact() and k2.intact() and n.intact(), hw
+        assert k1.written() and n.written(), hw
 
 
 def test_organised_outputs_stay_in_bounds(gpu, frames):
