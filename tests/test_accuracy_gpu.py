@@ -125,3 +125,32 @@ def test_torus_scene_parity(gpu, orc):
     assert rep.n_well_posed >= 0.56 * rep.n_valid_oracle, rep.summary()     # GB300: 0.585
     assert rep.frac_within_tol_all >= 0.77, rep.summary()                    # GB300: 0.789
     assert rep.max_normal_angle_well_posed < 1e-4, rep.summary()
+
+
+@pytest.mark.parametrize("r", [3, 7])
+def test_tilted_plane_has_zero_curvature(gpu, orc, r):
+    """The degenerate case of the shape operator: a noise-free tilted plane
+    (no curvature, so both eigenvalues 0 and T2 = hypot(0, 0)).  The only
+    error is the rounding of the stored ranges (about 1e-7 m), far below
+    0.05 m^-1 of curvature and 3e-5 rad of normal over the window; the oracle
+    agrees under the parity rule."""
+    from oracle import parity
+    n_true = np.array([0.3, -0.2, 1.0])
+    n_true /= np.linalg.norm(n_true)
+    cam = synth.kinect_camera(480, 640)
+    sc = synth.crop(synth.render(cam, [synth.Plane(n_true, 1.2)]), 200, 270, 70, 100)
+    k1, k2, n = run_gpu(gpu, sc, r)
+    m = interior(sc.label == 0, r)
+    assert m.sum() > 3000 and np.isfinite(k1[m]).all() and np.isfinite(k2[m]).all()
+    print("plane r", r, "max |k|", float(np.abs(k1[m]).max()), float(np.abs(k2[m]).max()))
+    assert np.abs(k1[m]).max() < 0.05 and np.abs(k2[m]).max() < 0.05
+    # angle by atan2(|n x t|, |n . t|): arccos of a dot product of single-precision
+    # unit vectors is only good to about sqrt(2e-7) = 4.5e-4 rad near zero
+    nm = n[m].astype(np.float64)
+    ang = np.arctan2(np.linalg.norm(np.cross(nm, n_true), axis=1), np.abs(nm @ n_true))
+    print("plane r", r, "max normal angle", float(ang.max()))
+    assert ang.max() < 3e-5, float(ang.max())      # range rounding 1e-7 m over a window of 7 mm: 1e-5 rad
+    p = orc.params(*sc.intrinsics, r=r, T=5, pivot_tol=PIVOT_TOL)
+    rep = parity.compare(k1, k2, n, parity.reference(sc.depth, p), pivot_tol=PIVOT_TOL)
+    print(rep.summary())
+    assert rep.ok(), rep.summary()

@@ -175,3 +175,47 @@ def test_benchmark_launch_sampled_against_oracle(gpu, orc):
         # them within tolerance (GB300)
         assert rep.ok() and rep.n_well_posed > 0.45 * rep.n_valid_oracle, rep.summary()
         assert rep.frac_within_tol_all > 0.90, rep.summary()
+
+
+def test_largest_batch(gpu):
+    """PC_MAX_BATCH frames in one call: four small crops of different sizes
+    and principal points, repeated; every frame equals its crop computed
+    alone, for the FP32 batch and the 16-bit storage batch."""
+    import torch
+    k = synth.kinect_scene(7)
+    crops = [synth.crop(k, 200, 300, H, W) for H, W in [(1, 1), (9, 33), (8, 32), (13, 17)]]
+    n = gpu.pcurv.PC_MAX_BATCH
+    c = gpu.Curvature(*crops[0].intrinsics, window_radius=7, iterations=5)
+    ref = per_frame(gpu, crops, 7, 5)
+    sizes = [crops[i % 4].depth.size for i in range(n)]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    k1, k2 = torch.full((int(offs[-1]),), 5.0, device="cuda"), torch.full((int(offs[-1]),), 5.0, device="cuda")
+    nrm = torch.full((3 * int(offs[-1]),), 5.0, device="cuda")
+    depth = [torch.from_numpy(s.depth).cuda() for s in crops]
+
+    def views(i):
+        H, W = crops[i % 4].depth.shape
+        a, b = int(offs[i]), int(offs[i + 1])
+        return k1[a:b].view(H, W), k2[a:b].view(H, W), nrm[3 * a:3 * b].view(H, W, 3)
+
+    def check(ref):
+        torch.cuda.synchronize()
+        h1, h2, hn = k1.cpu().numpy(), k2.cpu().numpy(), nrm.cpu().numpy()
+        for i in range(n):
+            a1, a2, an = ref[i % 4]
+            a, b = int(offs[i]), int(offs[i + 1])
+            assert same(a1.ravel(), h1[a:b]) and same(a2.ravel(), h2[a:b]) and same(an.ravel(), hn[3 * a:3 * b]), i
+
+    c.batch([(depth[i % 4], crops[i % 4].intrinsics, *views(i)) for i in range(n)])
+    check(ref)
+    for fmt in (1, 2):
+        packed = [c.pack(d, fmt) for d in depth]
+        ref = []
+        for s, (q, b) in zip(crops, packed):
+            cs = gpu.Curvature(*s.intrinsics, window_radius=7, iterations=5)
+            ref.append(tuple(x.cpu().numpy() for x in cs.compute_packed(q, b, fmt)))
+            cs.close()
+        k1.fill_(5.0), k2.fill_(5.0), nrm.fill_(5.0)
+        c.batch_packed([(*packed[i % 4], crops[i % 4].intrinsics, *views(i)) for i in range(n)], fmt)
+        check(ref)
+    c.close()
