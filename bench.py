@@ -19,7 +19,8 @@ normals inside the timed region, pipelined in chunks against the compute;
 the organised point cloud (pc_backproject, against the HBM peak) and the
 initial-normal field (pc_initial_normals); `roofline` reports the persistent
 kernel against the FP32 ALU peak; `cpu_baseline` times the FP64 oracle on a
-bounded sample on the host.
+bounded sample on the host, and the same leg's FP64 answers on one frame are
+what `precision` measures the precision variants against (rank 0, one GPU).
 
 --impl reference times the oracle alone, on the host cores, on the same
 workload (each step a bounded sample).
@@ -79,11 +80,10 @@ def parse(argv=None):
                     help="batches the continuous-batching server keeps on the GPU at once")
     ap.add_argument("--fp32-peak-seconds", type=float, default=1.0,
                     help="timed length of each form of the multiply-add microbenchmark")
-    ap.add_argument("--report", choices=["precision", "serve", "accuracy", "outputs", "table2", "sweep",
+    ap.add_argument("--report", choices=["serve", "accuracy", "outputs", "table2", "sweep",
                                          "tensorcore", "fp32peak"],
                     default=None,
-                    help="instead of the benchmark line: precision = error of each precision variant "
-                         "against the FP64 oracle (one 640x480 frame, radii 3, 7, 11); serve = the "
+                    help="instead of the benchmark line: serve = the "
                          "serving trace and a point at half capacity; accuracy = error against "
                          "analytic ground truth; outputs = the organised outputs alone; table2 = the "
                          "paper's timing grid (3 resolutions x 9x9, 21x21, sparse 37x37 windows); sweep = "
@@ -526,34 +526,40 @@ def outputs_report(curv, depth, stream, device_time, steps, sm_mhz):
     }
 
 
-def precision_report(args):
-    """Error of each precision variant against the FP64 oracle on one seeded
-    640x480 Kinect-like frame, per window radius, with its time per frame."""
-    from paper_1707_00385_gb300 import build as pcbuild
-    pcbuild.build()
-    return precision_rows((3, 7, 11), echo=True)
+# The precision variants the error columns cover: (name, context parameters,
+# 16-bit storage format); their pivot thresholds are PRECISION_PIVOTS.
+PRECISION_VARIANTS = [("fp32", {}, 0), ("fp32_kahan", {"kahan": 1}, 0),
+                      ("fp32_fp64solve", {"pivot_tol": 1e-7, "fp64_solve_cond": 1e6}, 0),
+                      ("fp16_storage", {}, 1), ("bf16_storage", {}, 2)]
+PRECISION_PIVOTS = (1e-5, 1e-7)
 
 
-def precision_rows(radii, echo=False):
-    """precision_report's rows for the given window radii (the GPU variants and
-    the FP64 oracle on frame 0 of the seeded scenes)."""
-    import torch
+def oracle_answers(depth, intr, radii, pivots=PRECISION_PIVOTS):
+    """Part of the cpu_baseline leg (rank 0, one GPU, host cores): the FP64
+    oracle's answers on one frame, which the precision columns measure the
+    GPU variants against.  Returns {(r, pivot): (k1, k2, valid)} as plain arrays."""
     import oracle
+    out = {}
+    for r in radii:
+        for piv in pivots:
+            f = oracle.curvature_image(depth, oracle.params(*intr, r=r, T=ITERS, pivot_tol=piv))
+            out[(r, piv)] = (f.k1, f.k2, f.status == oracle.OK)
+    return out
+
+
+def precision_rows(radii, refs, echo=False):
+    """Error of each precision variant on frame 0 of the seeded scenes against
+    refs = oracle_answers(frame 0, its intrinsics, radii), with its time per
+    frame: one row per variant and window radius."""
+    import torch
     import paper_1707_00385_gb300 as pc
     s = scenes(1)[0]
     intr = s.intrinsics
     d = torch.from_numpy(s.depth).cuda()
-    variants = [("fp32", {}, 0), ("fp32_kahan", {"kahan": 1}, 0),
-                ("fp32_fp64solve", {"pivot_tol": 1e-7, "fp64_solve_cond": 1e6}, 0),
-                ("fp16_storage", {}, 1), ("bf16_storage", {}, 2)]
     rows = []
     for r in radii:
-        ref = {}
-        for name, kw, fmt in variants:
-            piv = kw.get("pivot_tol", 1e-5)
-            if piv not in ref:
-                ref[piv] = oracle.curvature_image(s.depth, oracle.params(*intr, r=r, T=ITERS, pivot_tol=piv))
-            f = ref[piv]
+        for name, kw, fmt in PRECISION_VARIANTS:
+            fk1, fk2, ok = refs[(r, kw.get("pivot_tol", 1e-5))]
             c = pc.Curvature(*intr, window_radius=r, iterations=ITERS, **kw)
             if fmt:
                 packed, base = c.pack(d, fmt)
@@ -571,11 +577,10 @@ def precision_rows(radii, echo=False):
             torch.cuda.synchronize()
             k1, k2 = out[0].cpu().numpy(), out[1].cpu().numpy()
             c.close()
-            ok = f.status == oracle.OK
             both = ok & np.isfinite(k1)
-            err = np.maximum(np.abs(k1 - f.k1), np.abs(k2 - f.k2))[both]
-            rel = np.maximum(np.abs(k1 - f.k1) / (1e-4 + 1e-4 * np.abs(f.k1)),
-                             np.abs(k2 - f.k2) / (1e-4 + 1e-4 * np.abs(f.k2)))[both]
+            err = np.maximum(np.abs(k1 - fk1), np.abs(k2 - fk2))[both]
+            rel = np.maximum(np.abs(k1 - fk1) / (1e-4 + 1e-4 * np.abs(fk1)),
+                             np.abs(k2 - fk2) / (1e-4 + 1e-4 * np.abs(fk2)))[both]
             rows.append({"variant": name, "window_radius": r, "ms_per_frame": e0.elapsed_time(e1) / 10,
                          "valid_both": int(both.sum()), "validity_mismatch": int(np.sum(ok != np.isfinite(k1))),
                          "median_abs_dk": float(np.median(err)), "p99_abs_dk": float(np.quantile(err, 0.99)),
@@ -805,9 +810,6 @@ def main():
     if args.report == "table2":
         table2_report(args)
         return
-    if args.report == "precision":
-        precision_report(args)
-        return
     if args.report == "accuracy":
         accuracy_report(args)
         return
@@ -1017,8 +1019,14 @@ def main():
     # ---- host cost of one API call (what a per-frame caller pays beside the kernel)
     overhead = api_overhead(pc, curv, dev, stream)
 
-    # ---- precision variants against the FP64 oracle (one frame, radius 7)
-    precision = precision_rows((RADIUS,)) if rank == 0 else None
+    # ---- cpu_baseline leg (rank 0, one GPU): the FP64 oracle timed on the host
+    # cores, and its answers on frame 0 for the precision columns (radius 7)
+    cpu_leg = rank == 0 and world == 1 and not args.no_cpu_baseline
+    precision = None
+    if cpu_leg:
+        cpu_line = cpu_baseline([s.depth for s in sc], intr, args.cpu_seconds)
+        s0 = scenes(1)[0]
+        precision = precision_rows((RADIUS,), oracle_answers(s0.depth, s0.intrinsics, (RADIUS,)))
 
     # ---- roofline of the persistent kernel: counted FP32 work vs the FP32 ALU
     # ceiling, derived at the SM clock sampled during the timed region and
@@ -1060,8 +1068,8 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clocks,
             "roofline": roof}
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline([s.depth for s in sc], intr, args.cpu_seconds)
+    if cpu_leg:
+        line["cpu_baseline"] = cpu_line
     if rank == 0:
         print(json.dumps(line), flush=True)
     curv.close()

@@ -48,6 +48,8 @@ struct BatchScratch {
     int graph_variant[2] = {-1, -1};
     cudaStream_t capture = nullptr;           // private stream used only for capture
     int grid[pcurv::NUM_TILE_VARIANTS] = {};  // persistent CTAs per tile variant
+    const pcurv::KernelOps* packed_ops = nullptr;  // kernels packed_grid was sized for
+    int packed_grid = 0;                      // persistent CTAs of the 16-bit storage batch
     int next = 0;                             // staging copy of the next call
 };
 
@@ -184,7 +186,9 @@ void release_batch(BatchScratch& b) {
     if (b.capture) cudaStreamDestroy(b.capture);
     b.capture = nullptr;
     b.cap = 0;
-    b.grid[0] = b.grid[1] = 0;
+    for (int& g : b.grid) g = 0;
+    b.packed_ops = nullptr;
+    b.packed_grid = 0;
     b.device = -1;
 }
 
@@ -849,10 +853,15 @@ pc_status pc_compute_packed_batch(pc_ctx* ctx, const pc_packed_frame* frames, in
     pc_status st = ensure_batch(ctx, b, live);
     if (st != PC_OK) return st;
     const pcurv::KernelOps* ops = pcurv::select_packed_ops(ctx->cfg, format);
-    int sms = 0, per_sm = 0;
-    cudaError_t e = sm_count(ctx, &sms);
-    if (e == cudaSuccess) e = ops->occupancy[0](ctx->cfg, &per_sm);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "packed batch occupancy");
+    cudaError_t e;
+    if (b.packed_ops != ops) {  // sized once per kernel and device (ensure_batch resets it)
+        int sms = 0, per_sm = 0;
+        e = sm_count(ctx, &sms);
+        if (e == cudaSuccess) e = ops->occupancy[0](ctx->cfg, &per_sm);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "packed batch occupancy");
+        b.packed_grid = sms * (per_sm > 0 ? per_sm : 1);
+        b.packed_ops = ops;
+    }
     const int slot = b.next;
     b.next ^= 1;
     if (b.pending[slot]) {
@@ -876,7 +885,7 @@ pc_status pc_compute_packed_batch(pc_ctx* ctx, const pc_packed_frame* frames, in
     t->nframes = live;
     t->total_tiles = begin;
     cudaStream_t s = (cudaStream_t)stream;
-    const int slots = sms * (per_sm > 0 ? per_sm : 1);  // one CTA per tile when the queue is shorter
+    const int slots = b.packed_grid;  // one CTA per tile when the queue is shorter
     if ((e = cudaMemcpyAsync(b.d_table, t, pcurv::batch_table_bytes(live), cudaMemcpyHostToDevice, s)) !=
             cudaSuccess ||
         (e = cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned), s)) != cudaSuccess ||

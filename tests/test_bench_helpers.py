@@ -97,3 +97,16 @@ def test_cpu_model_is_named():
     import bench
     m = bench.cpu_model()
     assert isinstance(m, str) and m.strip()
+
+
+def test_oracle_answers_keys_and_shapes(orc):
+    """The cpu_baseline leg's FP64 answers for the precision columns: one
+    (k1, k2, valid) triple per window radius and pivot threshold."""
+    import synth
+    s = synth.crop(synth.kinect_scene(3), 200, 300, 12, 20)
+    refs = bench.oracle_answers(s.depth, s.intrinsics, (2, 3))
+    assert set(refs) == {(r, p) for r in (2, 3) for p in bench.PRECISION_PIVOTS}
+    for k1, k2, ok in refs.values():
+        assert k1.shape == k2.shape == ok.shape == (12, 20) and ok.dtype == bool
+        assert np.isfinite(k1[ok]).all() and np.all(k1[ok] >= k2[ok])
+    assert {p.get("pivot_tol", 1e-5) for _, p, _ in bench.PRECISION_VARIANTS} <= set(bench.PRECISION_PIVOTS)

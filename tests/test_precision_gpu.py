@@ -178,3 +178,26 @@ def test_storage_error_is_measured(gpu, orc, crop):
         med[fmt] = float(np.median(np.abs(k1[both] - ref.k1[both])))
     print("median |dk1| fp16 %.3g bf16 %.3g" % (med[1], med[2]))
     assert med[1] < med[2]
+
+
+def test_precision_table(gpu, orc):
+    """The error table of the precision variants (FP32, Kahan sums, FP64
+    solve fallback, FP16 and BF16 storage) against the FP64 oracle on one
+    640x480 frame at r = 3, 7, 11, printed as PRECISION_ROW lines.  What must
+    hold: compensated sums are at least as accurate as plain FP32, and the
+    16-bit storage kernels (unrolled at these radii) run at the FP32 path's
+    speed."""
+    import json
+    import bench
+    s = bench.scenes(1)[0]
+    radii = (3, 7, 11)
+    rows = bench.precision_rows(radii, bench.oracle_answers(s.depth, s.intrinsics, radii))
+    for row in rows:
+        print("PRECISION_ROW " + json.dumps(row))
+    by = {(d["variant"], d["window_radius"]): d for d in rows}
+    for r in radii:
+        fp32 = by[("fp32", r)]
+        assert by[("fp32_kahan", r)]["frac_within_tol"] >= fp32["frac_within_tol"] - 0.002, r
+        for v in ("fp16_storage", "bf16_storage"):
+            assert by[(v, r)]["ms_per_frame"] <= 1.15 * fp32["ms_per_frame"], (v, r)
+    assert by[("fp32", 7)]["frac_within_tol"] >= 0.92      # GB300: 0.940

@@ -44,6 +44,28 @@ def test_oracle_never_imports_the_package():
         assert not any(m.startswith("paper_1707_00385_gb300") or m == "bench" for m in mods), f
 
 
+def test_bench_runs_the_oracle_only_in_its_cpu_leg():
+    """bench.py imports the oracle only inside the functions of its
+    cpu_baseline leg (the timed host baseline, which --impl reference also
+    runs, and the FP64 answers the precision columns are measured against),
+    never at module level or on the device path."""
+    path = os.path.join(ROOT, "bench.py")
+    tree = ast.parse(open(path).read(), filename=path)
+    allowed = {"cpu_baseline", "oracle_answers"}
+    found = set()
+    for fn in ast.walk(tree):
+        if isinstance(fn, ast.FunctionDef):
+            for node in ast.walk(fn):
+                if isinstance(node, ast.Import) and any(a.name.split(".")[0] == "oracle" for a in node.names):
+                    found.add(fn.name)
+                if isinstance(node, ast.ImportFrom) and node.module and node.module.split(".")[0] == "oracle":
+                    found.add(fn.name)
+    top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
+    assert "oracle" not in {m for n in top for m in ([a.name.split(".")[0] for a in n.names]
+                                                     if isinstance(n, ast.Import) else [n.module.split(".")[0]])}
+    assert found == allowed, found
+
+
 def test_sources_include_nothing_of_the_other_side():
     cuda = glob.glob(os.path.join(PKG, "csrc", "*"))
     assert cuda
