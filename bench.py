@@ -54,6 +54,7 @@ FLOP_PER_NORMAL_PT = 12
 FP32_LANES_PER_SM = 128
 SERVE_REQUESTS = 20000       # the serving workload's trace (Poisson arrivals at 2000/s)
 SERVE_HALF_REQUESTS = 4000   # the trace offered at half the measured batched capacity
+SERVE_VERIFY = 100           # served requests whose results are checked after the timed traces
 # batches the continuous-batching server keeps on the GPU.  GB300, 3000 requests: 2 / 3 / 4 in
 # flight served 1403 / 1406 / 1390 frames/s at 2000/s offered, p99 6.57 / 5.91 / 5.56 ms at half
 # capacity (one launch per frame: 5.8-6.5 ms across the same runs)
@@ -372,10 +373,11 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def serve_trace(scenes_, n, rate, seed, batched=True, plain=True, inflight=SERVE_INFLIGHT):
+def serve_trace(scenes_, n, rate, seed, batched=True, plain=True, inflight=SERVE_INFLIGHT, verify=0):
     """Serves n requests arriving as a Poisson process at `rate` per second,
     each a frame drawn uniformly from scenes_ (host, page-locked), with the
-    continuous-batching server and with one launch per frame."""
+    continuous-batching server and with one launch per frame; then, when
+    verify > 0, checks the results of `verify` more served requests."""
     import torch
     from paper_1707_00385_gb300.serve import (GpuExecutor, PlainExecutor, Request, Server, device_budget,
                                               poisson_arrivals)
@@ -404,7 +406,35 @@ def serve_trace(scenes_, n, rate, seed, batched=True, plain=True, inflight=SERVE
         out[name] = {"frames_per_s": st.frames_per_s, "mpixel_per_s": st.mpixel_per_s, "p50_ms": st.p50_ms,
                      "p99_ms": st.p99_ms, "mean_batch": st.mean_batch, "batches": st.batches,
                      "peak_device_bytes": st.peak_device_bytes}
+    if batched and verify:
+        out["served_results"] = served_results_check(pool, rate, seed + 2000, verify, inflight)
     return out
+
+
+def served_results_check(pool, rate, seed, n, inflight):
+    """Untimed: n requests of the same mix served by the continuous-batching
+    server with their results kept, each compared with its frame computed
+    alone by pc_compute (the path the parity tests check against the FP64
+    oracle).  Equal bits mean the served answers carry exactly that path's
+    error against the oracle (the `precision` key)."""
+    import torch
+    import paper_1707_00385_gb300 as pc
+    from paper_1707_00385_gb300.serve import GpuExecutor, Request, Server, device_budget, poisson_arrivals
+    alone = []
+    for d, intr in pool:
+        c = pc.Curvature(*intr, window_radius=RADIUS, iterations=ITERS)
+        alone.append([x.cpu().numpy() for x in c(d.cuda())])
+        c.close()
+    t = poisson_arrivals(n, rate, seed)
+    pick = np.random.default_rng(seed).integers(0, len(pool), n)
+    ex = GpuExecutor(RADIUS, ITERS, slots=inflight, keep_results=True)
+    reqs = [Request(i, *pool[pick[i]], float(t[i])) for i in range(n)]
+    st = Server(ex, device_budget(0.5), max_batch_frames=64, inflight=inflight).run(reqs)
+    ex.close()
+    equal = all(r.error is None and all(np.array_equal(x.numpy(), y, equal_nan=True)
+                                        for x, y in zip((r.k1, r.k2, r.normal), alone[pick[r.rid]]))
+                for r in reqs)
+    return {"requests": n, "mean_batch": st.mean_batch, "equal_to_frame_alone": bool(equal)}
 
 
 def _interior(mask, r):
@@ -581,10 +611,14 @@ def precision_rows(radii, refs, echo=False):
             err = np.maximum(np.abs(k1 - fk1), np.abs(k2 - fk2))[both]
             rel = np.maximum(np.abs(k1 - fk1) / (1e-4 + 1e-4 * np.abs(fk1)),
                              np.abs(k2 - fk2) / (1e-4 + 1e-4 * np.abs(fk2)))[both]
+            # relative error with a floor of 1 m^-1 (flat surfaces have k near 0)
+            relk = np.maximum(np.abs(k1 - fk1) / np.maximum(np.abs(fk1), 1.0),
+                              np.abs(k2 - fk2) / np.maximum(np.abs(fk2), 1.0))[both]
             rows.append({"variant": name, "window_radius": r, "ms_per_frame": e0.elapsed_time(e1) / 10,
                          "valid_both": int(both.sum()), "validity_mismatch": int(np.sum(ok != np.isfinite(k1))),
                          "median_abs_dk": float(np.median(err)), "p99_abs_dk": float(np.quantile(err, 0.99)),
-                         "frac_within_tol": float(np.mean(rel <= 1))})
+                         "frac_within_tol": float(np.mean(rel <= 1)),
+                         "frac_rel_err_le_1e-3": float(np.mean(relk <= 1e-3))})
             if echo:
                 print(json.dumps(rows[-1]), flush=True)
     return rows
@@ -968,7 +1002,7 @@ def main():
     # batching vs one launch per frame (same frames, same trace): the stated
     # 20,000-request trace, then a shorter one offered at half the batched capacity
     serve_res = serve_trace(un, args.serve_requests if args.serve_requests is not None else SERVE_REQUESTS,
-                            args.serve_rate, seed=11, inflight=args.serve_inflight)
+                            args.serve_rate, seed=11, inflight=args.serve_inflight, verify=SERVE_VERIFY)
     half_rate = 0.5 * serve_res["continuous_batching"]["frames_per_s"]
     half_n = SERVE_HALF_REQUESTS if args.serve_requests is None else max(1, args.serve_requests // 5)
     serve_res["half_capacity"] = serve_trace(un, half_n, half_rate, seed=12, inflight=args.serve_inflight)
