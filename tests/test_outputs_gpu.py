@@ -94,7 +94,7 @@ def initial_normals(pc, depth, intr, **kw):
     return n.cpu().numpy()
 
 
-@pytest.mark.parametrize("nr", [1, 3, 5])
+@pytest.mark.parametrize("nr", [1, 3, 5, 8])
 def test_initial_normals_match_oracle(gpu, orc, scene, nr):
     from oracle import parity
     d = holes(scene.depth, 11)

@@ -109,6 +109,13 @@ def test_kinect_crop_other_k_and_normal_radius(gpu, orc, crop):
     check(gpu, orc, crop, 5, 4, min_well_posed=0.75, min_within=0.94, k=4e-4, normal_radius=2)
 
 
+def test_kinect_crop_largest_normal_radius(gpu, orc, crop):
+    """PC_MAX_NORMAL_RADIUS (17 x 17 initial-normal patch) around a 7 x 7
+    window: the staged halo is set by the normal patch, not the window."""
+    check(gpu, orc, crop, 3, 5, min_well_posed=0.80, min_within=0.94,     # GB300: 0.823, 0.964
+          normal_radius=gpu.pcurv.PC_MAX_NORMAL_RADIUS)
+
+
 def test_full_frame_sampled(gpu, orc, kinect640):
     """640 x 480, radius 7, 5 iterations (the benchmark's launch): 2500 random
     pixels plus two whole 32 x 8 tiles (a corner and an interior one)."""
