@@ -134,8 +134,9 @@ __global__ void __launch_bounds__(TILE_W * TH, 4 * 8 / TH)
         bool ok = Zp > 0.f;
         if (ok)
             ok = rn == NORMAL_RADIUS_UNROLLED
-                     ? initial_normal<NORMAL_RADIUS_UNROLLED>(tz + cidx, SW, 0, (float)u0 - cam.cx,
-                                                              (float)v0 - cam.cy, Zp, cam, det_tol, nx, ny, nz)
+                     ? initial_normal<NORMAL_RADIUS_UNROLLED, true>(tz + cidx, SW, 0, (float)u0 - cam.cx,
+                                                                    (float)v0 - cam.cy, Zp, cam, det_tol, nx, ny,
+                                                                    nz)
                      : initial_normal<0>(tz + cidx, SW, rn, (float)u0 - cam.cx, (float)v0 - cam.cy, Zp, cam,
                                          det_tol, nx, ny, nz);
         const size_t out = (size_t)v0 * W + u0;
