@@ -12,7 +12,7 @@ Prints one JSON line.  `value` is Mpixel/s over the device-timed region with
 inputs resident in HBM; `per_frame_launches` is the same with one pc_compute
 launch per frame; `uneven_batch` runs 64 frames of mixed resolutions
 (320x240, 512x424 time-of-flight, 640x480, 1280x720) in one batch call
-against 64 plain launches; `e2e` is the metric through pc_compute_host_batch
+against 64 plain launches, `small_frames` 512 frames of 64x48 likewise; `e2e` is the metric through pc_compute_host_batch
 with pinned host buffers (host-to-device ranges and device-to-host k1, k2,
 normals inside the timed region, pipelined in chunks against the compute;
 `one_call_per_frame` is pc_compute_host once per frame); `outputs` times
@@ -100,6 +100,17 @@ def scenes(n):
 
 
 UNEVEN_SIZES = [(240, 320, "kinect"), (424, 512, "tof"), (480, 640, "kinect"), (720, 1280, "kinect")]
+
+
+# Small frames: the size of the smallest parity case, cut from the seeded scenes.
+SMALL_H, SMALL_W = 48, 64
+SMALL_FRAMES = 512
+SMALL_DISTINCT = 16
+
+
+def synth_crop(scene, v0, u0, h, w):
+    import synth
+    return synth.crop(scene, v0, u0, h, w)
 
 
 def uneven_scenes(per_size=2):
@@ -998,6 +1009,34 @@ def main():
     for c_ in un_ctx:
         c_.close()
 
+    # ---- small frames (64x48, the size of the smallest parity case): 512 in one
+    # batch call vs one launch each, where one frame fills only 12 of 152 SMs
+    sm_scenes = [synth_crop(sc[i % nsc], 20 + 25 * i, 30 + 35 * i, SMALL_H, SMALL_W) for i in range(SMALL_DISTINCT)]
+    sm_dev = []
+    for i in range(SMALL_FRAMES):
+        s_ = sm_scenes[i % SMALL_DISTINCT]
+        d_ = torch.from_numpy(s_.depth).to(dev)
+        sm_dev.append((d_, s_.intrinsics, torch.empty_like(d_), torch.empty_like(d_),
+                       torch.empty(d_.shape + (3,), device=dev)))
+    sm_ctx = [pc.Curvature(*s_.intrinsics, window_radius=RADIUS, iterations=ITERS) for s_ in sm_scenes]
+
+    def step_sm_batch():
+        curv.batch(sm_dev, stream=stream)
+
+    def step_sm_frames():
+        for i, (d_, _, a_, b_, n_) in enumerate(sm_dev):
+            sm_ctx[i % SMALL_DISTINCT](d_, a_, b_, n_, stream=stream)
+
+    ms_sb = device_time(step_sm_batch, ub_steps)
+    ms_sf = device_time(step_sm_frames, ub_steps)
+    small = {"frames": SMALL_FRAMES, "size": f"{SMALL_W}x{SMALL_H}", "distinct_crops": SMALL_DISTINCT,
+             "inputs": "L2-resident (12 KB per frame)",
+             "batch_frames_per_s": whole_job_rate(world, SMALL_FRAMES * ub_steps, ms_sb / 1e3),
+             "plain_launch_frames_per_s": whole_job_rate(world, SMALL_FRAMES * ub_steps, ms_sf / 1e3),
+             "batch_ms": ms_sb / ub_steps, "plain_ms": ms_sf / ub_steps}
+    for c_ in sm_ctx:
+        c_.close()
+
     # ---- serving: Poisson arrivals of the mixed-resolution frames, continuous
     # batching vs one launch per frame (same frames, same trace): the stated
     # 20,000-request trace, then a shorter one offered at half the batched capacity
@@ -1096,6 +1135,7 @@ def main():
             "outputs": outputs,
             "per_frame_launches": {"value": pf_value, "unit": "Mpixel/s", "ms_per_frame": ms_pf / max(2, args.steps // 2) / F},
             "uneven_batch": uneven,
+            "small_frames": small,
             "serve": serve_res,
             "precision": precision,
             "api_overhead": overhead,
