@@ -95,6 +95,7 @@ class Reference:
     sens: np.ndarray         # sensitivity in units of the tolerance (inf: validity flips)
     amp: float
     flips: np.ndarray = None  # the oracle's validity changes in some probe run
+    f32_within: float = float("nan")  # the oracle with its sums in single precision: fraction within tolerance
 
 
 def reference(depth, p, nthreads=0, seeds=PROBE_SEEDS, uv=None) -> Reference:
@@ -106,6 +107,7 @@ def reference(depth, p, nthreads=0, seeds=PROBE_SEEDS, uv=None) -> Reference:
     t1, t2 = tolerance(f.k1), tolerance(f.k2)
     sens = np.zeros_like(f.k1)
     flips = np.zeros(f.k1.shape, bool)
+    f32_within = float("nan")
     probes = []
     for s in seeds:
         q = copy.copy(p)
@@ -120,9 +122,12 @@ def reference(depth, p, nthreads=0, seeds=PROBE_SEEDS, uv=None) -> Reference:
             d = np.maximum(np.abs(fp.k1 - f.k1) / t1, np.abs(fp.k2 - f.k2) / t2)
         flip = (fp.status == OK) != (f.status == OK)
         flips |= flip
+        if q.f32_sums:
+            both = (fp.status == OK) & (f.status == OK)
+            f32_within = float(np.mean(d[both] <= 1)) if both.any() else 1.0
         d[flip & (f.status == OK)] = np.inf
         sens = np.maximum(sens, np.nan_to_num(d, nan=0.0))
-    return Reference(f, sens, amp, flips)
+    return Reference(f, sens, amp, flips, f32_within)
 
 
 @dataclass
@@ -144,6 +149,7 @@ class Report:
     p999_rel_excluded: float = 0.0    # 99.9th percentile of |dk| / tol over them
     p99_excluded_over_spread: float = 0.0   # |dk| over the probe's own spread (sens), 99th percentile
     max_excluded_over_spread: float = 0.0   # and maximum, over the excluded pixels with a finite spread
+    frac_within_tol_f32_sums: float = float("nan")   # the oracle itself with single-precision sums
 
     def ok(self) -> bool:
         return self.n_validity_mismatch == 0 and self.n_well_posed_bad == 0 and self.nan_pattern_ok
@@ -158,7 +164,8 @@ class Report:
                 f"({self.n_cond_well_posed / max(self.n_valid_oracle, 1):.3f}) of which within tol "
                 f"{self.frac_within_tol_cond:.4f}; excluded {self.n_excluded}: max |dk|/tol "
                 f"{self.max_rel_excluded:.3g}, p99.9 {self.p999_rel_excluded:.3g}; over the probe's spread "
-                f"p99 {self.p99_excluded_over_spread:.3g}, max {self.max_excluded_over_spread:.3g}")
+                f"p99 {self.p99_excluded_over_spread:.3g}, max {self.max_excluded_over_spread:.3g}; "
+                f"the oracle with single-precision sums within tol {self.frac_within_tol_f32_sums:.4f}")
 
     def row(self) -> dict:
         """the figures of one parity case, for the committed summary"""
@@ -171,6 +178,7 @@ class Report:
                 "excluded": self.n_excluded, "max_excluded": self.max_rel_excluded,
                 "p999_excluded": self.p999_rel_excluded, "p99_excluded_over_spread": self.p99_excluded_over_spread,
                 "max_excluded_over_spread": self.max_excluded_over_spread,
+                "f32_sums_within": self.frac_within_tol_f32_sums,
                 "normal_angle": self.max_normal_angle_well_posed}
 
 
@@ -213,7 +221,7 @@ def compare(k1, k2, normal, ref: Reference, pivot_tol: float, band: float = 10.0
                   int(ex.sum()), float(rel[ex].max()) if ex.any() else 0.0,
                   float(np.quantile(rel[ex], 0.999)) if ex.any() else 0.0,
                   float(np.quantile(spread, 0.99)) if spread.size else 0.0,
-                  float(spread.max()) if spread.size else 0.0)
+                  float(spread.max()) if spread.size else 0.0, ref.f32_within)
 
 
 # ---- the initial-normal field on its own (Sec. 3.2.1) --------------------------

@@ -217,3 +217,24 @@ def test_tensor_core_moments_need_the_split(orc, noisy):
         within[mode] = float(np.mean(rel[both] <= 1))
     assert within[2] < within[1] - 0.1, within
     assert abs(within[3] - within[1]) < 0.02, within
+
+
+def test_reference_reports_the_single_precision_sums_floor(orc):
+    """parity.reference keeps, beside the spread, how many pixels the oracle
+    itself keeps within tolerance when its sums are formed in single precision
+    (the yardstick a single-precision kernel is read against): the same
+    fraction as a direct comparison of the two oracle runs."""
+    from oracle import parity
+    import synth
+    s = synth.crop(synth.kinect_scene(0), 180, 250, 24, 40)
+    p = orc.params(*s.intrinsics, r=5, T=5, pivot_tol=1e-5)
+    ref = parity.reference(s.depth, p)
+    f = orc.curvature_image(s.depth, p)
+    q = orc.params(*s.intrinsics, r=5, T=5, pivot_tol=1e-5)
+    q.f32_sums = 1
+    g = orc.curvature_image(s.depth, q)
+    both = (f.status == orc.OK) & (g.status == orc.OK)
+    rel = np.maximum(np.abs(g.k1 - f.k1) / parity.tolerance(f.k1), np.abs(g.k2 - f.k2) / parity.tolerance(f.k2))
+    assert both.sum() > 500
+    assert ref.f32_within == float(np.mean(rel[both] <= 1))
+    assert 0.5 < ref.f32_within < 1.0          # single-precision sums do move some answers
