@@ -124,6 +124,8 @@ def test_torus_scene_parity(gpu, orc):
     assert rep.ok(), rep.summary()
     assert rep.n_well_posed >= 0.56 * rep.n_valid_oracle, rep.summary()     # GB300: 0.585
     assert rep.frac_within_tol_all >= 0.77, rep.summary()                    # GB300: 0.789
+    # at least as many as the oracle with single-precision sums (GB300: 0.780)
+    assert rep.frac_within_tol_all >= rep.frac_within_tol_f32_sums - 0.005, rep.summary()
     assert rep.max_normal_angle_well_posed < 1e-4, rep.summary()
 
 

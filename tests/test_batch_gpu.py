@@ -175,6 +175,8 @@ def test_benchmark_launch_sampled_against_oracle(gpu, orc):
         # them within tolerance (GB300)
         assert rep.ok() and rep.n_well_posed > 0.45 * rep.n_valid_oracle, rep.summary()
         assert rep.frac_within_tol_all > 0.90, rep.summary()
+        # at least as many as the oracle with single-precision sums (GB300: 0.007-0.010 more)
+        assert rep.frac_within_tol_all >= rep.frac_within_tol_f32_sums - 0.005, rep.summary()
 
 
 def test_largest_batch(gpu):

@@ -84,6 +84,8 @@ def test_lane_group_against_oracle(gpu, orc, scenes, case, lanes):
     assert rep.n_well_posed_bad == 0, rep.summary()
     assert rep.n_well_posed >= min_wp * rep.n_valid_oracle, rep.summary()
     assert rep.frac_within_tol_all >= min_within, rep.summary()
+    # at least as many pixels within tolerance as the oracle with single-precision sums
+    assert rep.frac_within_tol_all >= rep.frac_within_tol_f32_sums - 0.005, rep.summary()
     assert rep.max_normal_angle_well_posed < 1e-4, rep.summary()
 
 

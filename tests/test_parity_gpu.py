@@ -19,6 +19,11 @@ import synth
 pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
 
 PIVOT_TOL = 1e-5
+# The oracle itself, with its sums formed in single precision (plain loop
+# order, everything else FP64), keeps a fraction of the pixels within the
+# tolerance; the CUDA path must keep at least as many, up to this slack (GB300:
+# at or above it in every case but the 64-iteration one, 0.0012 below).
+F32_SLACK = 0.005
 
 
 @pytest.fixture(scope="module")
@@ -61,6 +66,7 @@ def check(pc, orc, scene, r, T, min_well_posed, min_within, uv=None, **params):
     assert rep.n_well_posed_bad == 0, rep.summary()
     assert rep.n_well_posed >= min_well_posed * rep.n_valid_oracle, rep.summary()
     assert rep.frac_within_tol_all >= min_within, rep.summary()
+    assert rep.frac_within_tol_all >= rep.frac_within_tol_f32_sums - F32_SLACK, rep.summary()
     assert rep.max_normal_angle_well_posed < 1e-4, rep.summary()
     return rep
 
@@ -147,6 +153,7 @@ def test_full_frame_every_pixel_batched(gpu, orc, kinect640):
     assert rep.ok(), rep.summary()
     assert rep.n_well_posed >= 0.72 * rep.n_valid_oracle, rep.summary()     # 0.745 of the oracle's pixels
     assert rep.frac_within_tol_all >= 0.93, rep.summary()                    # GB300: 0.940
+    assert rep.frac_within_tol_all >= rep.frac_within_tol_f32_sums - F32_SLACK, rep.summary()   # 0.931
     assert rep.max_normal_angle_well_posed < 1e-4, rep.summary()
 
 
